@@ -1,0 +1,206 @@
+/*
+ * pet_gb300.h -- C ABI of the GB300 (sm_103a) library for the subset-gradient path
+ * of RDP-regularised PET reconstruction with preconditioned SGD / SAGA / SVRG
+ * (Ehrhardt, Kereta, Schramm, "Fast PET Reconstruction with Variance Reduction and
+ * Prior-Aware Preconditioning").
+ *
+ * Conventions for every entry point
+ *   - Pointers named x, q, g, out, D, grad, hdiag, y, r, mu, sens_lor, kappa, ref are
+ *     DEVICE pointers owned by the caller; the library never frees them.  Pointers to
+ *     pet_geometry / option structs and the z1/z2 / order / pc_iters arrays are HOST
+ *     pointers read during the call only.
+ *   - Images are float32, layout [nz][ny][nx] (x fastest); voxel (ix,iy,iz) has centre
+ *     ((ix-(nx-1)/2) dx, (iy-(ny-1)/2) dy, (iz-(nz-1)/2) dz) in mm.
+ *   - Sinograms are laid out [view][plane][radial][tof]; a subset's compact sinogram
+ *     is [j][plane][radial][tof] over its views v = s, s+n, s+2n, ... (Sec. 3.1: subsets
+ *     are every n-th view).  Per-LOR arrays (sens_lor, m) drop the tof axis.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  All
+ *     work is enqueued asynchronously on it; results are valid once the stream has
+ *     reached that point.  Scalar results (double*) are device pointers too.
+ *   - Every call returns a pet_status; no exception or abort crosses the ABI.
+ *     Argument errors are detected on the host before anything is enqueued.  A data
+ *     infeasibility seen by a kernel (ybar <= 0 where y > 0) is recorded in a device
+ *     error word and reported by pet_plan_check().
+ */
+#ifndef PET_GB300_H
+#define PET_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PET_OK = 0,
+  PET_ERR_ARG = 1,         /* null pointer, out-of-range index or option */
+  PET_ERR_SHAPE = 2,       /* geometry that the projector cannot represent */
+  PET_ERR_INFEASIBLE = 3,  /* ybar <= 0 with y > 0: KL term infinite (Sec. 1.2) */
+  PET_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
+  PET_ERR_CUDA = 5,        /* a CUDA runtime call failed */
+  PET_ERR_UNSUPPORTED = 6, /* valid but not implemented (e.g. > 32 TOF bins) */
+  PET_ERR_STATE = 7,       /* call order violated (e.g. data not set) */
+  PET_ERR_NOMEM = 8        /* device allocation failed */
+} pet_status;
+
+typedef enum { PET_Y_U16 = 0, PET_Y_U32 = 1, PET_Y_F32 = 2 } pet_ytype;
+
+typedef struct pet_plan pet_plan;
+typedef struct pet_solver pet_solver;
+
+/* Scanner and image description (forward model of Sec. 1.1 eq. 1; simulated
+ * cylindrical scanner of Sec. 3.1).  View v has angle v*pi/nview; radial bin r sits at
+ * signed distance (r-(nrad-1)/2)*drad from the axis; plane p joins axial positions
+ * z1[p] (endpoint 1) and z2[p] (endpoint 2) on a cylinder of radius rdet (mm).
+ * ntof <= 1 means non-TOF; otherwise bin b of width tof_bin (mm) is centred at
+ * (b-(ntof-1)/2)*tof_bin from the LOR midpoint toward endpoint 2 and the timing
+ * kernel is a Gaussian of std tof_sigma (mm) truncated at 3 sigma.  nsubsets is the
+ * number n of view subsets (eq. 2). */
+typedef struct {
+  int nx, ny, nz;
+  double dx, dy, dz;
+  int nrad, nview, nplane, ntof;
+  double drad, rdet;
+  const double *z1, *z2;
+  double tof_sigma, tof_bin;
+  int nsubsets;
+} pet_geometry;
+
+/* Relative difference prior (eq. 3) parameters.  Outputs of pet_rdp are scaled by
+ * `scale` (pass beta for beta*S, beta/n for the per-subset share of eq. 5).  Weights:
+ * w_ij = min(dx,dy,dz) / |offset (mm)| over the 26-neighbourhood (8 in-plane when
+ * nz == 1); neighbours outside the image are omitted.  kappa: device image or NULL. */
+typedef struct {
+  int nx, ny, nz;
+  double dx, dy, dz;
+  float gamma, eps, scale;
+  const float *kappa;
+} pet_rdp_params;
+
+/* ---------------------------------------------------------------- plan */
+
+/* Validates the geometry (every LOR must have |s| < rdet and an in-plane driving
+ * axis), builds the per-view / per-LOR / per-plane tables on the current device and
+ * allocates the plan's scratch.  Returns PET_ERR_SHAPE or PET_ERR_UNSUPPORTED for a
+ * geometry the projector cannot represent, PET_ERR_NOMEM on allocation failure. */
+pet_status pet_plan_create(const pet_geometry *geom, pet_plan **out);
+void pet_plan_destroy(pet_plan *plan);
+
+/* Binds the measured data (borrowed: y [V][P][R][T] of type yt, r [V][P][R][T] float32)
+ * and computes the multiplicative factors m = sens_lor * exp(-P mu) per LOR (Sec. 1.1:
+ * A includes sensitivities and attenuation; mu in 1/mm, NULL = none; sens_lor NULL =
+ * 1) and the sensitivity images A^T 1 and A_s^T 1 (Sec. 2.3).  The caller keeps y and
+ * r alive while the plan uses them.  Synchronises `stream` before returning. */
+pet_status pet_plan_set_data(pet_plan *plan, const void *y, pet_ytype yt, const float *r,
+                             const float *mu, const float *sens_lor, void *stream);
+
+/* Number of views of subset s (s = -1: all views). */
+pet_status pet_subset_size(const pet_plan *plan, int subset, int *nviews);
+
+/* Multiplicative factors m [V][P][R] computed by pet_plan_set_data (device pointer
+ * owned by the plan, valid until destroy). */
+const float *pet_plan_mult(const pet_plan *plan);
+
+/* Sensitivity image A_s^T 1 (s = -1: all views) owned by the plan. */
+const float *pet_plan_sensitivity(const pet_plan *plan, int subset);
+
+/* Reads and clears the device error word after synchronising `stream`: PET_OK or
+ * PET_ERR_INFEASIBLE. */
+pet_status pet_plan_check(pet_plan *plan, void *stream);
+
+/* ---------------------------------------------------------------- operators */
+
+/* out = A_s x (Joseph forward projection of subset s, TOF-weighted when ntof > 1,
+ * times m), compact subset layout.  eq. 5 needs A_s x for f_s. */
+pet_status pet_forward(pet_plan *plan, int subset, const float *x, float *out, void *stream);
+
+/* g = A_s^T q (matched transpose of pet_forward; q in compact subset layout).
+ * deterministic = 0: ray-driven scatter with atomics (summation order varies run to
+ * run); 1: voxel-driven gather with compensated sums in a fixed order (bitwise
+ * reproducible). */
+pet_status pet_back(pet_plan *plan, int subset, const float *q, float *g, int deterministic,
+                    void *stream);
+
+/* Subset objective f_s(x) = D_s(x) + scale_prior * S(x) and its gradient (eq. 5):
+ * g = A_s^T (1 - y/(A_s x + r)) [+ prior->scale * grad S(x)].  prior may be NULL (data
+ * term only).  obj (device double, may be NULL) receives f_s(x) summed in FP64.
+ * flags: PET_GRAD_DETERMINISTIC uses the deterministic backprojector;
+ * PET_OBJ_ONLY skips the backprojection (g untouched; recompute mode).  s = -1: all views. */
+#define PET_GRAD_DETERMINISTIC 1
+#define PET_OBJ_ONLY 2
+pet_status pet_objective_grad(pet_plan *plan, int subset, const float *x, float *g, double *obj,
+                              const pet_rdp_params *prior, int flags, void *stream);
+
+/* One OSEM sub-iteration on subset s (MLEM for nsubsets = 1), in place:
+ * x <- x / (A_s^T 1) * A_s^T (y_s / (A_s x + r_s)); voxels with A_s^T 1 = 0 keep their
+ * value (Sec. 3.1 initialises runs with one OSEM epoch). */
+pet_status pet_em_update(pet_plan *plan, int subset, float *x, void *stream);
+
+/* RDP gradient, Hessian diagonal and value (eq. 3, Appendix A.1), each scaled by
+ * p->scale: grad = scale dS/dx, hdiag = scale d2S/dx2, val = scale S (FP64).  Any of
+ * grad, hdiag, val may be NULL.  accumulate != 0 adds into grad instead of writing. */
+pet_status pet_rdp(const pet_rdp_params *p, const float *x, float *grad, float *hdiag,
+                   double *val, int accumulate, void *stream);
+
+/* Diagonal preconditioner of Sec. 2.3 with delta = delta_rel * max(x):
+ * hdiag_betaS == NULL: D_MLEM = (x+delta)/A^T 1;
+ * otherwise the harmonic form of eq. 8: (x+delta)/(A^T 1 + alpha hdiag_betaS (x+delta)).
+ * Entries with a zero denominator are 0. */
+pet_status pet_precond(pet_plan *plan, const float *x, const float *hdiag_betaS, float alpha,
+                       float delta_rel, float *D, void *stream);
+
+/* NRMSE of Sec. 3.1: sqrt(mean over mask of (x-ref)^2) / mean over bg of ref, FP64;
+ * mask and bg are device uint8 images; out is a device double. */
+pet_status pet_nrmse(const float *x, const float *ref, const uint8_t *mask, const uint8_t *bg,
+                     size_t n, double *out, void *stream);
+
+/* ---------------------------------------------------------------- solver */
+
+typedef enum { PET_SGD = 0, PET_SAGA = 1, PET_SVRG = 2 } pet_algo;
+typedef enum {
+  PET_STEP_CONST = 0,  /* tau0 */
+  PET_STEP_VANISH = 1, /* tau0 / (1 + eta k / n)          (Sec. 2.2) */
+  PET_STEP_ALG1 = 2,   /* piecewise 3, 2, 1.5, 1, 0.5      (Table 1, ALG1) */
+  PET_STEP_BB = 3,     /* short Barzilai-Borwein p'q/q'q at SVRG refreshes (Sec. 2.2) */
+  PET_STEP_ALG2 = 4    /* BB capped at 3 / 2.2 / 1         (Table 1, ALG2/3) */
+} pet_step_rule;
+
+/* Options of the preconditioned proximal stochastic gradient method (eq. 6) with
+ * the SGD, SAGA (eq. 7) or SVRG (eq. 9, Algorithm 1) estimator. */
+typedef struct {
+  int algo;               /* pet_algo */
+  int omega;              /* SVRG snapshot period in epochs (default 2, Sec. 2.1) */
+  int step_rule;          /* pet_step_rule */
+  double tau0, eta;       /* constant / vanishing parameters; BB start value */
+  int precond_kind;       /* 0 D_MLEM, 1 harmonic (eq. 8) */
+  double alpha;           /* harmonic weight */
+  double delta_rel;       /* delta = delta_rel * max(x) at each preconditioner update */
+  const long long *pc_iters; int n_pc; /* iterations that recompute D (Algorithm 1) */
+  float beta, gamma, eps; /* RDP strength and shape (eq. 3, eq. 4) */
+  const float *kappa;     /* device image or NULL */
+  unsigned long long seed;/* subset order: splitmix64-driven Fisher-Yates per epoch */
+  const int *order;       /* host, optional explicit subset per iteration (overrides seed) */
+  long long norder;
+  int use_graph;          /* capture each epoch in a CUDA graph */
+  int deterministic;      /* deterministic backprojector */
+} pet_solver_opts;
+
+pet_status pet_solver_create(pet_plan *plan, const pet_solver_opts *opts, pet_solver **out);
+void pet_solver_destroy(pet_solver *s);
+/* Copies the start image (device) into the solver; resets iteration count and tables. */
+pet_status pet_solver_set_image(pet_solver *s, const float *x, void *stream);
+/* Device pointer to the current iterate (owned by the solver, valid until the next run). */
+const float *pet_solver_image(const pet_solver *s);
+/* Runs niter further iterations of eq. 6 (Algorithm 1 for SVRG). */
+pet_status pet_solver_run(pet_solver *s, long long niter, void *stream);
+/* Host copy of the stepsizes used so far (up to cap entries); returns the count. */
+long long pet_solver_taus(const pet_solver *s, double *taus, long long cap);
+long long pet_solver_iteration(const pet_solver *s);
+
+const char *pet_status_str(pet_status st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -153,6 +153,16 @@ def project(G: Geometry, x, views=None):
     return out
 
 
+def project_lors(G: Geometry, x, vpr):
+    """Geometric projection of listed LORs; vpr is an (L, 3) int array of (view, plane, radial)."""
+    vpr = np.ascontiguousarray(vpr, np.int32)
+    x = _f64(x)
+    out = np.zeros((len(vpr), G.T))
+    if lib().o_project_lors(G.ref, _i(vpr), len(vpr), _d(x), _d(out)) != 0:
+        raise ValueError("axial axis would drive a LOR")
+    return out
+
+
 def backproject(G: Geometry, q, views=None):
     views = np.arange(G.s.nview, dtype=np.int32) if views is None else np.asarray(views, np.int32)
     q = _f64(q)

@@ -181,6 +181,29 @@ int o_project(const og_geom *g, const int *views, int nviews, const double *x, d
   return rc;
 }
 
+/* Geometric projection of an explicit list of LORs (v, p, r triples): out[l][b]. */
+int o_project_lors(const og_geom *g, const int *vpr, int nl, const double *x, double *out) {
+  int me = max_entries(g);
+  int *vox = malloc(sizeof(int) * me);
+  double *wt = malloc(sizeof(double) * me), *tp = malloc(sizeof(double) * me);
+  int T = g->ntof > 1 ? g->ntof : 1;
+  int rc = 0;
+  for (int l = 0; l < nl; l++) {
+    int ne = o_lor_entries(g, vpr[3 * l], vpr[3 * l + 1], vpr[3 * l + 2], vox, wt, tp);
+    if (ne < 0) { rc = -1; ne = 0; }
+    for (int b = 0; b < T; b++) {
+      double acc = 0.0;
+      for (int e = 0; e < ne; e++) {
+        double tw = (T > 1) ? o_tof_weight(g, b, tp[e]) : 1.0;
+        acc += wt[e] * tw * x[vox[e]];
+      }
+      out[(size_t)l * T + b] = acc;
+    }
+  }
+  free(vox); free(wt); free(tp);
+  return rc;
+}
+
 /* Literal transpose of o_project: img = P^T q (img is overwritten). */
 int o_backproject(const og_geom *g, const int *views, int nviews, const double *q, double *img) {
   int me = max_entries(g);

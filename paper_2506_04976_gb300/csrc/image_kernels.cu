@@ -1,0 +1,267 @@
+// Image-domain kernels for sm_103a: the 26-neighbour relative difference prior
+// (eq. 3; gradient and Hessian diagonal of Appendix A.1) as a 3D stencil with halo
+// tiles in shared memory, deterministic FP64 reductions, the diagonal preconditioners
+// of Sec. 2.3 (eq. 8), the EM update and the NRMSE of Sec. 3.1.
+#include <math.h>
+
+#include "pet_internal.cuh"
+
+namespace petgb {
+
+constexpr int RDP_TX = 32, RDP_TY = 8, RDP_ZCH = 8;
+
+RdpArgs make_rdp_args(const pet_rdp_params &p) {
+  RdpArgs a;
+  a.nx = p.nx; a.ny = p.ny; a.nz = p.nz;
+  const double dmin = fmin(p.dx, fmin(p.dy, p.dz));
+  const int off[7][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}};
+  for (int k = 0; k < 7; ++k) {
+    const double ex = off[k][0] * p.dx, ey = off[k][1] * p.dy, ez = off[k][2] * p.dz;
+    a.w[k] = (float)(dmin / sqrt(ex * ex + ey * ey + ez * ez));
+  }
+  a.gamma = p.gamma; a.eps = p.eps; a.scale = p.scale; a.kappa = p.kappa;
+  return a;
+}
+
+int rdp_blocks(int nx, int ny, int nz) {
+  return ((nx + RDP_TX - 1) / RDP_TX) * ((ny + RDP_TY - 1) / RDP_TY) * ((nz + RDP_ZCH - 1) / RDP_ZCH);
+}
+
+__device__ __forceinline__ double block_sum_d(double v) {
+  __shared__ double red[32];
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthreads = blockDim.x * blockDim.y;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (tid < 32) {
+    s = tid < (nthreads >> 5) ? red[tid] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  return s;  // valid in thread 0
+}
+
+template <bool KAPPA>
+__global__ void __launch_bounds__(RDP_TX * RDP_TY) k_rdp(RdpArgs a, const float *__restrict__ x,
+                                                          float *__restrict__ grad, float *__restrict__ hdiag,
+                                                          double *__restrict__ val_part, int accumulate) {
+  __shared__ float sx[3][RDP_TY + 2][RDP_TX + 2];
+  __shared__ float sk[KAPPA ? 3 : 1][RDP_TY + 2][RDP_TX + 2];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * RDP_TX + tx;
+  const int nbx = (a.nx + RDP_TX - 1) / RDP_TX, nby = (a.ny + RDP_TY - 1) / RDP_TY;
+  const int bx = blockIdx.x % nbx, by = (blockIdx.x / nbx) % nby, bz = blockIdx.x / (nbx * nby);
+  const int x0 = bx * RDP_TX, y0 = by * RDP_TY;
+  const int z0 = bz * RDP_ZCH, z1 = min(a.nz, z0 + RDP_ZCH);
+  const int nxy = a.nx * a.ny;
+
+  auto load_plane = [&](int z) {
+    const int slot = (z + 3) % 3;
+    for (int e = tid; e < (RDP_TY + 2) * (RDP_TX + 2); e += RDP_TX * RDP_TY) {
+      const int ly = e / (RDP_TX + 2), lx = e % (RDP_TX + 2);
+      const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+      float v = 0.f, kv = 0.f;
+      if (z >= 0 && z < a.nz && gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny) {
+        const size_t gi = (size_t)z * nxy + (size_t)gy * a.nx + gx;
+        v = __ldg(x + gi);
+        if (KAPPA) kv = __ldg(a.kappa + gi);
+      }
+      sx[slot][ly][lx] = v;
+      if (KAPPA) sk[slot][ly][lx] = kv;
+    }
+  };
+
+  double vsum = 0.0;
+  load_plane(z0 - 1);
+  load_plane(z0);
+  const int gx = x0 + tx, gy = y0 + ty;
+  for (int z = z0; z < z1; ++z) {
+    load_plane(z + 1);
+    __syncthreads();
+    if (gx < a.nx && gy < a.ny) {
+      const int sc = (z + 3) % 3;
+      const float xi = sx[sc][ty + 1][tx + 1];
+      const float ki = KAPPA ? sk[sc][ty + 1][tx + 1] : 1.f;
+      float gsum = 0.f, hsum = 0.f, vs = 0.f;
+#pragma unroll
+      for (int oz = -1; oz <= 1; ++oz) {
+        const int jz = z + oz;
+        if (jz < 0 || jz >= a.nz) continue;
+        const int sl = (jz + 3) % 3;
+#pragma unroll
+        for (int oy = -1; oy <= 1; ++oy) {
+          if (gy + oy < 0 || gy + oy >= a.ny) continue;
+#pragma unroll
+          for (int ox = -1; ox <= 1; ++ox) {
+            if (ox == 0 && oy == 0 && oz == 0) continue;
+            if (gx + ox < 0 || gx + ox >= a.nx) continue;
+            constexpr int widx[8] = {-1, 0, 1, 3, 2, 4, 5, 6};
+            const int code = (ox != 0 ? 1 : 0) + (oy != 0 ? 2 : 0) + (oz != 0 ? 4 : 0);
+            float w = a.w[widx[code]];
+            const float xj = sx[sl][ty + 1 + oy][tx + 1 + ox];
+            if (KAPPA) w *= ki * sk[sl][ty + 1 + oy][tx + 1 + ox];
+            const float d = xi - xj;
+            const float ad = fabsf(d);
+            const float phi = (xi + xj) + a.gamma * ad + a.eps;
+            const float inv = __frcp_rn(phi);
+            const float inv2 = inv * inv;
+            gsum = fmaf(w * d * ((2.f * phi - d) - a.gamma * ad), inv2, gsum);
+            const float e2 = fmaf(2.f, xj, a.eps);
+            hsum = fmaf(2.f * w * e2 * e2, inv2 * inv, hsum);
+            vs = fmaf(w * d * d, inv, vs);
+          }
+        }
+      }
+      const size_t gi = (size_t)z * nxy + (size_t)gy * a.nx + gx;
+      if (grad) grad[gi] = accumulate ? fmaf(a.scale, gsum, grad[gi]) : a.scale * gsum;
+      if (hdiag) hdiag[gi] = a.scale * hsum;
+      vsum += 0.5 * (double)vs;
+    }
+    __syncthreads();
+  }
+  if (val_part) {
+    const double s = block_sum_d(vsum * (double)a.scale);
+    if (tid == 0) val_part[blockIdx.x] = s;
+  }
+}
+
+cudaError_t launch_rdp(const RdpArgs &a, const float *x, float *grad, float *hdiag,
+                       double *val_part, int accumulate, int *nblocks_out, cudaStream_t st) {
+  const int nb = rdp_blocks(a.nx, a.ny, a.nz);
+  if (nblocks_out) *nblocks_out = nb;
+  dim3 block(RDP_TX, RDP_TY);
+  if (a.kappa) k_rdp<true><<<nb, block, 0, st>>>(a, x, grad, hdiag, val_part, accumulate);
+  else k_rdp<false><<<nb, block, 0, st>>>(a, x, grad, hdiag, val_part, accumulate);
+  return cudaGetLastError();
+}
+
+// Deterministic sum of n partials: fixed strided order per thread, fixed tree.
+__global__ void k_reduce_sum(const double *__restrict__ part, int n, double *out, int accumulate) {
+  __shared__ double s[1024];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = accumulate ? *out + s[0] : s[0];
+}
+
+cudaError_t launch_reduce_sum(const double *part, int n, double *out, int accumulate,
+                              cudaStream_t st) {
+  k_reduce_sum<<<1, 1024, 0, st>>>(part, n, out, accumulate);
+  return cudaGetLastError();
+}
+
+int max_blocks(size_t n) { return (int)min((size_t)1024, (n + 1023) / 1024); }
+
+__global__ void k_max_part(const float *__restrict__ x, size_t n, float *part) {
+  __shared__ float s[256];
+  float m = -INFINITY;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, x[i]);
+  s[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) s[threadIdx.x] = fmaxf(s[threadIdx.x], s[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+__global__ void k_max_final(const float *part, int n, float *out) {
+  __shared__ float s[1024];
+  float m = -INFINITY;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, part[i]);
+  s[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) s[threadIdx.x] = fmaxf(s[threadIdx.x], s[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+cudaError_t launch_max(const float *x, size_t n, float *part, float *out, cudaStream_t st) {
+  const int nb = max_blocks(n);
+  k_max_part<<<nb, 256, 0, st>>>(x, n, part);
+  k_max_final<<<1, 1024, 0, st>>>(part, nb, out);
+  return cudaGetLastError();
+}
+
+// D = (x+delta)/(sens + alpha h (x+delta)), delta = delta_rel * max(x); h == NULL: MLEM.
+__global__ void k_precond(const float *__restrict__ x, const float *__restrict__ sens,
+                          const float *__restrict__ h, float alpha, const float *xmax, float delta_rel,
+                          float *__restrict__ D, size_t n) {
+  const float delta = delta_rel * fmaxf(*xmax, 0.f);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float num = x[i] + delta;
+    float den = sens[i];
+    if (h) den = fmaf(alpha * h[i], num, den);
+    D[i] = den > 0.f ? num / den : 0.f;
+  }
+}
+
+static unsigned grid_1d(size_t n) { return (unsigned)min((size_t)152 * 16, (n + 255) / 256); }
+
+cudaError_t launch_precond(const float *x, const float *sens, const float *hdiag, float alpha,
+                           const float *xmax, float delta_rel, float *D, size_t n,
+                           cudaStream_t st) {
+  k_precond<<<grid_1d(n), 256, 0, st>>>(x, sens, hdiag, alpha, xmax, delta_rel, D, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_em_apply(float *__restrict__ x, const float *__restrict__ bp,
+                           const float *__restrict__ sens, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float s = sens[i];
+    if (s > 0.f) x[i] = x[i] / s * bp[i];
+  }
+}
+
+cudaError_t launch_em_apply(float *x, const float *bp, const float *sens, size_t n,
+                            cudaStream_t st) {
+  k_em_apply<<<grid_1d(n), 256, 0, st>>>(x, bp, sens, n);
+  return cudaGetLastError();
+}
+
+int nrmse_blocks(size_t n) { return (int)min((size_t)1024, (n + 1023) / 1024); }
+
+__global__ void k_nrmse_part(const float *__restrict__ x, const float *__restrict__ ref,
+                             const uint8_t *__restrict__ mask, const uint8_t *__restrict__ bg, size_t n,
+                             double *part) {
+  double se = 0, nm = 0, sb = 0, nb = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if (mask[i]) { const double d = (double)x[i] - (double)ref[i]; se += d * d; nm += 1; }
+    if (bg[i]) { sb += ref[i]; nb += 1; }
+  }
+  double r;
+  r = block_sum_d(se); if (threadIdx.x == 0) part[4 * blockIdx.x + 0] = r;
+  r = block_sum_d(nm); if (threadIdx.x == 0) part[4 * blockIdx.x + 1] = r;
+  r = block_sum_d(sb); if (threadIdx.x == 0) part[4 * blockIdx.x + 2] = r;
+  r = block_sum_d(nb); if (threadIdx.x == 0) part[4 * blockIdx.x + 3] = r;
+}
+
+__global__ void k_nrmse_final(const double *part, int nb, double *out) {
+  if (threadIdx.x != 0) return;
+  double se = 0, nm = 0, sb = 0, nbg = 0;
+  for (int b = 0; b < nb; ++b) {
+    se += part[4 * b]; nm += part[4 * b + 1]; sb += part[4 * b + 2]; nbg += part[4 * b + 3];
+  }
+  *out = sqrt(se / nm) / (sb / nbg);
+}
+
+cudaError_t launch_nrmse(const float *x, const float *ref, const uint8_t *mask, const uint8_t *bg,
+                         size_t n, double *part, double *out, cudaStream_t st) {
+  const int nb = nrmse_blocks(n);
+  k_nrmse_part<<<nb, 256, 0, st>>>(x, ref, mask, bg, n, part);
+  k_nrmse_final<<<1, 32, 0, st>>>(part, nb, out);
+  return cudaGetLastError();
+}
+
+}  // namespace petgb

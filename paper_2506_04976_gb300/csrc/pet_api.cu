@@ -1,0 +1,348 @@
+// Host side of the C ABI declared in include/pet_gb300.h: plan construction (geometry
+// tables in the driving frame of each view), data binding (attenuation factors and
+// sensitivity images), and the operator entry points.  Every entry point validates its
+// arguments on the host, enqueues kernels on the caller's stream and returns a status.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "pet_internal.cuh"
+#include "pet_plan.h"
+
+using namespace petgb;
+
+#define PET_CK(call)                                  \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return PET_ERR_CUDA;       \
+  } while (0)
+
+extern "C" const char *pet_status_str(pet_status st) {
+  switch (st) {
+    case PET_OK: return "ok";
+    case PET_ERR_ARG: return "invalid argument";
+    case PET_ERR_SHAPE: return "geometry not representable";
+    case PET_ERR_INFEASIBLE: return "infeasible data: ybar <= 0 where y > 0";
+    case PET_ERR_TIMEOUT: return "bounded device wait timed out";
+    case PET_ERR_CUDA: return "CUDA runtime error";
+    case PET_ERR_UNSUPPORTED: return "unsupported configuration";
+    case PET_ERR_STATE: return "invalid call order";
+    case PET_ERR_NOMEM: return "device allocation failed";
+  }
+  return "unknown status";
+}
+
+static cudaStream_t S(void *st) { return (cudaStream_t)st; }
+
+template <class T>
+static cudaError_t dalloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return cudaSuccess;
+  return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+// Driving axis of view v: x when |u_x|/dx >= |u_y|/dy, u = (-sin phi, cos phi).  For
+// square pixels the comparison is the exact integer test V <= 4v <= 3V.
+static int view_xdrive(const pet_geometry &g, int v) {
+  if (g.dx == g.dy) return (4 * v >= g.nview && 4 * v <= 3 * g.nview) ? 1 : 0;
+  const double phi = v * M_PI / g.nview;
+  return fabs(sin(phi)) * g.dy >= fabs(cos(phi)) * g.dx ? 1 : 0;
+}
+
+static void plan_free(pet_plan *p) {
+  if (!p) return;
+  cudaFree(p->d_view); cudaFree(p->d_vr); cudaFree(p->d_plane); cudaFree(p->d_aff);
+  cudaFree(p->d_m); cudaFree(p->d_sens); cudaFree(p->d_sens_sub);
+  cudaFree(p->d_xT); cudaFree(p->d_gT); cudaFree(p->d_part); cudaFree(p->d_err);
+  cudaFree(p->d_fpart); cudaFree(p->d_fscalar); cudaFree(p->d_qtmp); cudaFree(p->d_img);
+  delete p;
+}
+
+extern "C" pet_status pet_plan_create(const pet_geometry *geom, pet_plan **out) {
+  if (!geom || !out) return PET_ERR_ARG;
+  *out = nullptr;
+  const pet_geometry &g = *geom;
+  if (g.nx < 1 || g.ny < 1 || g.nz < 1 || g.nrad < 1 || g.nview < 1 || g.nplane < 1) return PET_ERR_ARG;
+  if (!(g.dx > 0 && g.dy > 0 && g.dz > 0 && g.drad > 0 && g.rdet > 0)) return PET_ERR_ARG;
+  if (!g.z1 || !g.z2) return PET_ERR_ARG;
+  if (g.nsubsets < 1 || g.nsubsets > g.nview) return PET_ERR_ARG;
+  if (g.ntof > 32) return PET_ERR_UNSUPPORTED;
+  if (g.ntof > 1 && !(g.tof_sigma > 0 && g.tof_bin > 0)) return PET_ERR_ARG;
+  const long long nvox = (long long)g.nx * g.ny * g.nz;
+  const long long nlor = (long long)g.nview * g.nplane * g.nrad;
+  if (nvox >= (1LL << 31) || nlor >= (1LL << 31)) return PET_ERR_UNSUPPORTED;
+  const double smax = 0.5 * (g.nrad - 1) * g.drad;
+  if (!(smax < g.rdet)) return PET_ERR_SHAPE;
+
+  const int V = g.nview, R = g.nrad, P = g.nplane;
+  std::vector<float4> view(V), vr((size_t)V * R), plane(P);
+  std::vector<float2> aff(V);
+  double maxdz = 0.0;
+  for (int p = 0; p < P; ++p) maxdz = std::max(maxdz, fabs(g.z2[p] - g.z1[p]));
+  for (int v = 0; v < V; ++v) {
+    const double phi = v * M_PI / V, c = cos(phi), s = sin(phi);
+    const int xd = view_xdrive(g, v);
+    const double ua = xd ? -s : c, ub = xd ? c : -s;
+    const double da = xd ? g.dx : g.dy, db = xd ? g.dy : g.dx;
+    const int Na = xd ? g.nx : g.ny, Nb = xd ? g.ny : g.nx;
+    const double a0 = -0.5 * (Na - 1) * da;
+    view[v] = make_float4((float)xd, (float)(da * (ub / ua) / db), (float)(da / ua), 0.f);
+    double fb_r0 = 0, fb_r1 = 0;
+    for (int r = 0; r < R; ++r) {
+      const double sr = (r - 0.5 * (R - 1)) * g.drad;
+      const double h = sqrt(g.rdet * g.rdet - sr * sr);
+      // the axial axis must never drive: |dz|/dz_vox <= 2h|u_a|/delta_a
+      if (maxdz / g.dz > 2.0 * h * fabs(ua) / da) return PET_ERR_SHAPE;
+      const double Ma = xd ? sr * c : sr * s, Mb = xd ? sr * s : sr * c;
+      const double fb0 = (Mb + (a0 - Ma) * (ub / ua)) / db + 0.5 * (Nb - 1);
+      const double t0b = (a0 - Ma) / ua;
+      vr[(size_t)v * R + r] = make_float4((float)fb0, (float)t0b, (float)(1.0 / (2.0 * h)), 0.f);
+      if (r == 0) fb_r0 = fb0;
+      if (r == 1) fb_r1 = fb0;
+    }
+    const double slope = R > 1 ? fb_r1 - fb_r0 : 1.0;
+    aff[v] = make_float2((float)fb_r0, (float)(slope != 0.0 ? slope : 1.0));
+  }
+  for (int p = 0; p < P; ++p) {
+    const double zs = (g.z1[p] + g.z2[p]) / (2.0 * g.dz) + 0.5 * (g.nz - 1);
+    const double zd = (g.z2[p] - g.z1[p]) / g.dz;
+    plane[p] = make_float4((float)zs, (float)zd, (float)(g.z2[p] - g.z1[p]), 0.f);
+  }
+
+  pet_plan *pl = new pet_plan();
+  pl->g = g;
+  pl->z1.assign(g.z1, g.z1 + P);
+  pl->z2.assign(g.z2, g.z2 + P);
+  pl->g.z1 = pl->z1.data();
+  pl->g.z2 = pl->z2.data();
+  pl->N = (size_t)nvox;
+  pl->T = g.ntof > 1 ? g.ntof : 1;
+  cudaGetDevice(&pl->device);
+  pl->vs_max = (V + g.nsubsets - 1) / g.nsubsets;
+
+  DevPlan &dp = pl->dp;
+  memset(&dp, 0, sizeof(dp));
+  dp.nx = g.nx; dp.ny = g.ny; dp.nz = g.nz;
+  dp.nrad = R; dp.nview = V; dp.nplane = P; dp.T = pl->T; dp.nsub = g.nsubsets;
+  if (pl->T > 1) {
+    const double amax = 3.0 / sqrt(2.0);
+    dp.tof_inv = (float)(1.0 / (sqrt(2.0) * g.tof_sigma));
+    dp.tof_e0 = (float)(-0.5 * pl->T * g.tof_bin);
+    dp.tof_w = (float)g.tof_bin;
+    dp.tof_amax = (float)amax;
+    dp.tof_erfc_amax = (float)erfc(amax);
+    dp.tof_half_norm = (float)(1.0 / (2.0 * erf(amax)));
+  }
+  const int gb_all = grad_blocks(dp, V);
+  const int rb = ratio_blocks(dp, -1);
+  pl->npart = std::max({gb_all, rb, rdp_blocks(g.nx, g.ny, g.nz), 4 * nrmse_blocks(pl->N), 1});
+  bool ok = dalloc(&pl->d_view, V) == cudaSuccess && dalloc(&pl->d_vr, (size_t)V * R) == cudaSuccess &&
+            dalloc(&pl->d_plane, P) == cudaSuccess && dalloc(&pl->d_aff, V) == cudaSuccess &&
+            dalloc(&pl->d_m, (size_t)nlor) == cudaSuccess && dalloc(&pl->d_sens, pl->N) == cudaSuccess &&
+            dalloc(&pl->d_sens_sub, pl->N * g.nsubsets) == cudaSuccess &&
+            dalloc(&pl->d_xT, pl->N) == cudaSuccess && dalloc(&pl->d_gT, pl->N) == cudaSuccess &&
+            dalloc(&pl->d_img, pl->N) == cudaSuccess &&
+            dalloc(&pl->d_part, (size_t)pl->npart) == cudaSuccess && dalloc(&pl->d_err, 1) == cudaSuccess &&
+            dalloc(&pl->d_fpart, (size_t)max_blocks(pl->N)) == cudaSuccess &&
+            dalloc(&pl->d_fscalar, 4) == cudaSuccess;
+  if (!ok) { plan_free(pl); return PET_ERR_NOMEM; }
+  if (cudaMemcpy(pl->d_view, view.data(), V * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(pl->d_vr, vr.data(), vr.size() * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(pl->d_plane, plane.data(), P * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(pl->d_aff, aff.data(), V * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(pl->d_err, 0, sizeof(int)) != cudaSuccess) {
+    plan_free(pl);
+    return PET_ERR_CUDA;
+  }
+  dp.view = pl->d_view; dp.vr = pl->d_vr; dp.plane = pl->d_plane;
+  dp.m = pl->d_m; dp.err = pl->d_err;
+  pl->dd.view_aff = pl->d_aff;
+  *out = pl;
+  return PET_OK;
+}
+
+extern "C" void pet_plan_destroy(pet_plan *plan) { plan_free(plan); }
+
+extern "C" const float *pet_plan_mult(const pet_plan *plan) { return plan ? plan->d_m : nullptr; }
+
+extern "C" const float *pet_plan_sensitivity(const pet_plan *plan, int subset) {
+  if (!plan || subset < -1 || subset >= plan->g.nsubsets) return nullptr;
+  return subset < 0 ? plan->d_sens : plan->d_sens_sub + plan->N * (size_t)subset;
+}
+
+extern "C" pet_status pet_subset_size(const pet_plan *plan, int subset, int *nviews) {
+  if (!plan || !nviews || subset < -1 || subset >= plan->g.nsubsets) return PET_ERR_ARG;
+  *nviews = subset < 0 ? plan->g.nview
+                       : (plan->g.nview - subset + plan->g.nsubsets - 1) / plan->g.nsubsets;
+  return PET_OK;
+}
+
+namespace petgb {
+// x (canonical) -> plan scratch xT (x fastest becomes y fastest)
+cudaError_t to_frames(pet_plan *p, const float *x, cudaStream_t st) {
+  return launch_transpose(x, p->d_xT, p->g.nx, p->g.ny, p->g.nz, 0, 0, st);
+}
+// g += transpose(gT), leaving gT zeroed
+cudaError_t from_frames(pet_plan *p, float *g, cudaStream_t st) {
+  return launch_transpose(p->d_gT, g, p->g.nx, p->g.ny, p->g.nz, 1, 2, st);
+}
+cudaError_t zero_accumulators(pet_plan *p, float *g, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(g, 0, p->N * sizeof(float), st);
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(p->d_gT, 0, p->N * sizeof(float), st);
+}
+}  // namespace petgb
+
+extern "C" pet_status pet_plan_set_data(pet_plan *plan, const void *y, pet_ytype yt, const float *r,
+                                        const float *mu, const float *sens_lor, void *stream) {
+  if (!plan || !y || !r || (int)yt < 0 || (int)yt > 2) return PET_ERR_ARG;
+  cudaStream_t st = S(stream);
+  DevPlan &dp = plan->dp;
+  dp.y = y;
+  dp.yt = (int)yt;
+  dp.r = r;
+  if (mu) PET_CK(launch_transpose(mu, plan->d_xT, plan->g.nx, plan->g.ny, plan->g.nz, 0, 0, st));
+  PET_CK(launch_mult(dp, mu, plan->d_xT, sens_lor, plan->d_m, st));
+  // sensitivity images with the deterministic backprojector (ones)
+  PET_CK(launch_back_det(dp, plan->dd, -1, nullptr, plan->d_sens, 1, st));
+  for (int s = 0; s < plan->g.nsubsets; ++s)
+    PET_CK(launch_back_det(dp, plan->dd, s, nullptr, plan->d_sens_sub + plan->N * (size_t)s, 1, st));
+  PET_CK(cudaStreamSynchronize(st));
+  plan->has_data = true;
+  return PET_OK;
+}
+
+extern "C" pet_status pet_plan_check(pet_plan *plan, void *stream) {
+  if (!plan) return PET_ERR_ARG;
+  int h = 0;
+  PET_CK(cudaStreamSynchronize(S(stream)));
+  PET_CK(cudaMemcpy(&h, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  PET_CK(cudaMemset(plan->d_err, 0, sizeof(int)));
+  return h ? PET_ERR_INFEASIBLE : PET_OK;
+}
+
+static bool bad_subset(const pet_plan *p, int s) { return s < -1 || s >= p->g.nsubsets; }
+
+extern "C" pet_status pet_forward(pet_plan *plan, int subset, const float *x, float *out, void *stream) {
+  if (!plan || !x || !out || bad_subset(plan, subset)) return PET_ERR_ARG;
+  if (!plan->has_data) return PET_ERR_STATE;
+  cudaStream_t st = S(stream);
+  PET_CK(to_frames(plan, x, st));
+  PET_CK(launch_forward(plan->dp, subset, x, plan->d_xT, out, st));
+  return PET_OK;
+}
+
+extern "C" pet_status pet_back(pet_plan *plan, int subset, const float *q, float *g, int deterministic,
+                               void *stream) {
+  if (!plan || !q || !g || bad_subset(plan, subset)) return PET_ERR_ARG;
+  if (!plan->has_data) return PET_ERR_STATE;
+  cudaStream_t st = S(stream);
+  if (deterministic) {
+    PET_CK(launch_back_det(plan->dp, plan->dd, subset, q, g, 0, st));
+    return PET_OK;
+  }
+  PET_CK(zero_accumulators(plan, g, st));
+  PET_CK(launch_back(plan->dp, subset, q, g, plan->d_gT, st));
+  PET_CK(from_frames(plan, g, st));
+  return PET_OK;
+}
+
+// Compact-sinogram temporary for the deterministic objective path, grown on demand.
+static pet_status ensure_qtmp(pet_plan *p, int subset) {
+  const int nv = subset < 0 ? p->g.nview : p->vs_max;
+  const size_t n = (size_t)nv * p->g.nplane * p->g.nrad * p->T;
+  if (p->qtmp_cap >= n) return PET_OK;
+  cudaFree(p->d_qtmp);
+  p->d_qtmp = nullptr;
+  p->qtmp_cap = 0;
+  if (dalloc(&p->d_qtmp, n) != cudaSuccess) return PET_ERR_NOMEM;
+  p->qtmp_cap = n;
+  return PET_OK;
+}
+
+extern "C" pet_status pet_objective_grad(pet_plan *plan, int subset, const float *x, float *g, double *obj,
+                                         const pet_rdp_params *prior, int flags, void *stream) {
+  if (!plan || !x || bad_subset(plan, subset)) return PET_ERR_ARG;
+  const bool obj_only = (flags & PET_OBJ_ONLY) != 0;
+  if (!obj_only && !g) return PET_ERR_ARG;
+  if (!plan->has_data) return PET_ERR_STATE;
+  if (prior && (prior->nx != plan->g.nx || prior->ny != plan->g.ny || prior->nz != plan->g.nz))
+    return PET_ERR_ARG;
+  cudaStream_t st = S(stream);
+  PET_CK(to_frames(plan, x, st));
+  int nparts = 0;
+  if (flags & PET_GRAD_DETERMINISTIC && !obj_only) {
+    pet_status e = ensure_qtmp(plan, subset);
+    if (e != PET_OK) return e;
+    float *ax = plan->d_qtmp;
+    PET_CK(launch_forward(plan->dp, subset, x, plan->d_xT, ax, st));
+    nparts = ratio_blocks(plan->dp, subset);
+    PET_CK(launch_ratio(plan->dp, subset, ax, ax, obj ? plan->d_part : nullptr, MODE_GRAD, st));
+    PET_CK(launch_back_det(plan->dp, plan->dd, subset, ax, g, 0, st));
+  } else {
+    if (!obj_only) PET_CK(zero_accumulators(plan, g, st));
+    PET_CK(launch_grad(plan->dp, subset, nullptr, x, plan->d_xT, g, plan->d_gT, obj ? plan->d_part : nullptr,
+                       obj_only ? MODE_OBJ : MODE_GRAD, &nparts, st));
+    if (!obj_only) PET_CK(from_frames(plan, g, st));
+  }
+  if (obj) PET_CK(launch_reduce_sum(plan->d_part, nparts, obj, 0, st));
+  if (prior) {
+    RdpArgs a = make_rdp_args(*prior);
+    int nb = 0;
+    PET_CK(launch_rdp(a, x, obj_only ? nullptr : g, nullptr, obj ? plan->d_part : nullptr, 1, &nb, st));
+    if (obj) PET_CK(launch_reduce_sum(plan->d_part, nb, obj, 1, st));
+  }
+  return PET_OK;
+}
+
+extern "C" pet_status pet_em_update(pet_plan *plan, int subset, float *x, void *stream) {
+  if (!plan || !x || subset < 0 || subset >= plan->g.nsubsets) return PET_ERR_ARG;
+  if (!plan->has_data) return PET_ERR_STATE;
+  cudaStream_t st = S(stream);
+  float *bp = plan->d_img;
+  PET_CK(to_frames(plan, x, st));
+  PET_CK(zero_accumulators(plan, bp, st));
+  PET_CK(launch_grad(plan->dp, subset, nullptr, x, plan->d_xT, bp, plan->d_gT, nullptr, MODE_EM, nullptr, st));
+  PET_CK(from_frames(plan, bp, st));
+  PET_CK(launch_em_apply(x, bp, plan->d_sens_sub + plan->N * (size_t)subset, plan->N, st));
+  return PET_OK;
+}
+
+extern "C" pet_status pet_rdp(const pet_rdp_params *p, const float *x, float *grad, float *hdiag,
+                              double *val, int accumulate, void *stream) {
+  if (!p || !x || p->nx < 1 || p->ny < 1 || p->nz < 1) return PET_ERR_ARG;
+  cudaStream_t st = S(stream);
+  RdpArgs a = make_rdp_args(*p);
+  double *part = nullptr;
+  const int nb = rdp_blocks(p->nx, p->ny, p->nz);
+  if (val && cudaMallocAsync((void **)&part, nb * sizeof(double), st) != cudaSuccess) return PET_ERR_NOMEM;
+  cudaError_t e = launch_rdp(a, x, grad, hdiag, part, accumulate, nullptr, st);
+  if (e == cudaSuccess && val) e = launch_reduce_sum(part, nb, val, 0, st);
+  if (part) cudaFreeAsync(part, st);
+  return e == cudaSuccess ? PET_OK : PET_ERR_CUDA;
+}
+
+extern "C" pet_status pet_precond(pet_plan *plan, const float *x, const float *hdiag_betaS, float alpha,
+                                  float delta_rel, float *D, void *stream) {
+  if (!plan || !x || !D) return PET_ERR_ARG;
+  if (!plan->has_data) return PET_ERR_STATE;
+  cudaStream_t st = S(stream);
+  PET_CK(launch_max(x, plan->N, plan->d_fpart, plan->d_fscalar, st));
+  PET_CK(launch_precond(x, plan->d_sens, hdiag_betaS, alpha, plan->d_fscalar, delta_rel, D, plan->N, st));
+  return PET_OK;
+}
+
+extern "C" pet_status pet_nrmse(const float *x, const float *ref, const uint8_t *mask, const uint8_t *bg,
+                                size_t n, double *out, void *stream) {
+  if (!x || !ref || !mask || !bg || !out || n == 0) return PET_ERR_ARG;
+  cudaStream_t st = S(stream);
+  double *part = nullptr;
+  const int nb = nrmse_blocks(n);
+  if (cudaMallocAsync((void **)&part, 4 * nb * sizeof(double), st) != cudaSuccess) return PET_ERR_NOMEM;
+  cudaError_t e = launch_nrmse(x, ref, mask, bg, n, part, out, st);
+  cudaFreeAsync(part, st);
+  return e == cudaSuccess ? PET_OK : PET_ERR_CUDA;
+}

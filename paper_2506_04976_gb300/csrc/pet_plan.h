@@ -1,0 +1,39 @@
+// Host-side plan object behind the opaque pet_plan handle.
+#pragma once
+
+#include <vector>
+
+#include "pet_internal.cuh"
+
+struct pet_plan {
+  pet_geometry g;             // copy; z1/z2 point into the vectors below
+  std::vector<double> z1, z2;
+  size_t N = 0;               // voxels
+  int T = 1;                  // TOF bins (1: non-TOF)
+  int vs_max = 0;             // views in the largest subset
+  int device = 0;
+  bool has_data = false;
+  petgb::DevPlan dp;
+  petgb::DevPlanDet dd;
+  // geometry tables
+  float4 *d_view = nullptr, *d_vr = nullptr, *d_plane = nullptr;
+  float2 *d_aff = nullptr;
+  // derived data
+  float *d_m = nullptr;         // [V][P][R] multiplicative factors
+  float *d_sens = nullptr;      // [N] A^T 1
+  float *d_sens_sub = nullptr;  // [n][N] A_s^T 1
+  // scratch: driving-frame image and gradient (x-driven views), image temp, partials
+  float *d_xT = nullptr, *d_gT = nullptr, *d_img = nullptr;
+  double *d_part = nullptr;
+  int npart = 0;
+  int *d_err = nullptr;
+  float *d_fpart = nullptr, *d_fscalar = nullptr;
+  float *d_qtmp = nullptr;
+  size_t qtmp_cap = 0;
+};
+
+namespace petgb {
+cudaError_t to_frames(pet_plan *p, const float *x, cudaStream_t st);
+cudaError_t from_frames(pet_plan *p, float *g, cudaStream_t st);
+cudaError_t zero_accumulators(pet_plan *p, float *g, cudaStream_t st);
+}  // namespace petgb

@@ -1,0 +1,481 @@
+// Joseph ray-driven projector kernels for sm_103a: forward projection, matched
+// ray-driven backprojection, the fused subset gradient (forward -> KL ratio -> back,
+// eq. 5 with the KL data term of Sec. 1.2) and the setup kernels (attenuation factors,
+// sensitivity).  One thread owns one LOR; adjacent threads own adjacent radial bins of
+// the same view and plane, so their samples at a given plane touch adjacent voxels of
+// the driving-frame image.
+#include "pet_internal.cuh"
+
+namespace petgb {
+
+// ----------------------------------------------------------------- helpers
+__device__ __forceinline__ void kahan_add(float &sum, float &c, float v) {
+  const float yk = v - c;
+  const float tk = sum + yk;
+  c = (tk - sum) - yk;
+  sum = tk;
+}
+
+__device__ __forceinline__ float bilinear(const float *__restrict__ img, const Samp &S, int plane) {
+  const float v00 = (S.z0 && S.b0) ? __ldg(img + S.base) : 0.f;
+  const float v01 = (S.z0 && S.b1) ? __ldg(img + S.base + 1) : 0.f;
+  const float v10 = (S.z1 && S.b0) ? __ldg(img + S.base + plane) : 0.f;
+  const float v11 = (S.z1 && S.b1) ? __ldg(img + S.base + plane + 1) : 0.f;
+  return (1.f - S.wz) * ((1.f - S.wb) * v00 + S.wb * v01) + S.wz * ((1.f - S.wb) * v10 + S.wb * v11);
+}
+
+__device__ __forceinline__ void scatter(float *__restrict__ g, const Samp &S, int plane, float val) {
+  const float a0 = (1.f - S.wz) * val, a1 = S.wz * val;
+  if (S.z0 && S.b0) atomicAdd(g + S.base, (1.f - S.wb) * a0);
+  if (S.z0 && S.b1) atomicAdd(g + S.base + 1, S.wb * a0);
+  if (S.z1 && S.b0) atomicAdd(g + S.base + plane, (1.f - S.wb) * a1);
+  if (S.z1 && S.b1) atomicAdd(g + S.base + plane + 1, S.wb * a1);
+}
+
+// Number of TOF bins known at compile time (1: non-TOF; 11, 13: exact; 16, 32: bound).
+template <int TT>
+__device__ __forceinline__ int tof_bins(const DevPlan &P) {
+  return (TT == 1 || TT == 11 || TT == 13) ? TT : P.T;
+}
+
+// Forward: acc[b] = sum over samples of bilinear(x) * w_b(t) (compensated); the step
+// length L is applied by the caller.
+template <int TT>
+__device__ __forceinline__ void forward_lor(const DevPlan &P, const Lor &L,
+                                            const float *__restrict__ img, float (&acc)[TT]) {
+  const int Na = L.xdrive ? P.nx : P.ny;
+  const int Nb = L.xdrive ? P.ny : P.nx;
+  const int plane = Na * Nb;
+  const int T = tof_bins<TT>(P);
+  float cmp[TT];
+#pragma unroll
+  for (int b = 0; b < TT; ++b) { acc[b] = 0.f; cmp[b] = 0.f; }
+  const float du = P.tof_w * P.tof_inv;
+  for (int i = L.i0; i <= L.i1; ++i) {
+    Samp S;
+    sample_at(L, i, Na, Nb, P.nz, S);
+    const float val = bilinear(img, S, plane);
+    if (TT == 1) {
+      kahan_add(acc[0], cmp[0], val);
+    } else {
+      const float t = fmaf((float)i, L.dt, L.t0);
+      const float u0 = (P.tof_e0 - t) * P.tof_inv;
+      float uprev = u0, Gprev = tof_edge_G(P, u0);
+#pragma unroll
+      for (int k = 1; k <= TT; ++k) {
+        if (k <= T) {
+          const float u = fmaf((float)k, du, u0);
+          const float G = tof_edge_G(P, u);
+          const float w = tof_bin_weight(P, uprev, Gprev, u, G);
+          kahan_add(acc[k - 1], cmp[k - 1], val * w);
+          uprev = u;
+          Gprev = G;
+        }
+      }
+    }
+  }
+}
+
+// Back: scatter sum_b q[b] w_b(t) * bilinear weights; q already includes m and L.
+template <int TT>
+__device__ __forceinline__ void back_lor(const DevPlan &P, const Lor &L, float *__restrict__ img,
+                                         const float (&q)[TT]) {
+  const int Na = L.xdrive ? P.nx : P.ny;
+  const int Nb = L.xdrive ? P.ny : P.nx;
+  const int plane = Na * Nb;
+  const int T = tof_bins<TT>(P);
+  const float du = P.tof_w * P.tof_inv;
+  for (int i = L.i0; i <= L.i1; ++i) {
+    Samp S;
+    sample_at(L, i, Na, Nb, P.nz, S);
+    float val;
+    if (TT == 1) {
+      val = q[0];
+    } else {
+      const float t = fmaf((float)i, L.dt, L.t0);
+      const float u0 = (P.tof_e0 - t) * P.tof_inv;
+      float uprev = u0, Gprev = tof_edge_G(P, u0);
+      val = 0.f;
+#pragma unroll
+      for (int k = 1; k <= TT; ++k) {
+        if (k <= T) {
+          const float u = fmaf((float)k, du, u0);
+          const float G = tof_edge_G(P, u);
+          val = fmaf(q[k - 1], tof_bin_weight(P, uprev, Gprev, u, G), val);
+          uprev = u;
+          Gprev = G;
+        }
+      }
+    }
+    if (val != 0.f) scatter(img, S, plane, val);
+  }
+}
+
+struct LorIdx {
+  int v, p, r, l;
+  bool ok;
+};
+
+__device__ __forceinline__ LorIdx lor_index(const DevPlan &P, int subset, long long l) {
+  LorIdx o;
+  const int nsub = subset < 0 ? 1 : P.nsub;
+  const int s = subset < 0 ? 0 : subset;
+  const int nv = (P.nview - s + nsub - 1) / nsub;
+  const long long per_view = (long long)P.nplane * P.nrad;
+  o.ok = l < (long long)nv * per_view;
+  if (!o.ok) return o;
+  o.r = (int)(l % P.nrad);
+  const long long t = l / P.nrad;
+  o.p = (int)(t % P.nplane);
+  const int jv = (int)(t / P.nplane);
+  o.v = s + jv * nsub;
+  o.l = (int)l;
+  return o;
+}
+
+// ----------------------------------------------------------------- kernels
+template <int TT>
+__global__ void __launch_bounds__(kBlock) k_forward(DevPlan P, int subset, const float *__restrict__ x,
+                                                    const float *__restrict__ xT, float *__restrict__ out) {
+  const LorIdx id = lor_index(P, subset, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+  if (!id.ok) return;
+  Lor L;
+  lor_setup(P, id.v, id.p, id.r, L);
+  float acc[TT];
+  forward_lor<TT>(P, L, L.xdrive ? xT : x, acc);
+  const int T = tof_bins<TT>(P);
+  const float m = __ldg(&P.m[((size_t)id.v * P.nplane + id.p) * P.nrad + id.r]) * L.L;
+#pragma unroll
+  for (int b = 0; b < TT; ++b)
+    if (b < T) out[(size_t)id.l * T + b] = acc[b] * m;
+}
+
+template <int TT>
+__global__ void __launch_bounds__(kBlock) k_back(DevPlan P, int subset, const float *__restrict__ q,
+                                                 float *__restrict__ g, float *__restrict__ gT) {
+  const LorIdx id = lor_index(P, subset, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+  if (!id.ok) return;
+  Lor L;
+  lor_setup(P, id.v, id.p, id.r, L);
+  const int T = tof_bins<TT>(P);
+  const float m = __ldg(&P.m[((size_t)id.v * P.nplane + id.p) * P.nrad + id.r]) * L.L;
+  float qq[TT];
+  bool any = false;
+#pragma unroll
+  for (int b = 0; b < TT; ++b) {
+    qq[b] = b < T ? __ldg(&q[(size_t)id.l * T + b]) * m : 0.f;
+    any |= qq[b] != 0.f;
+  }
+  if (any) back_lor<TT>(P, L, L.xdrive ? gT : g, qq);
+}
+
+__device__ __forceinline__ void block_sum_store(double v, double *out) {
+  __shared__ double red[kBlock / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) *out = v;
+  }
+}
+
+// Fused subset gradient: forward, KL ratio, backprojection; optional FP64 KL partials.
+template <int TT>
+__global__ void __launch_bounds__(kBlock) k_grad(DevPlan P, int subset, const int *subset_dev,
+                                                 const float *__restrict__ x, const float *__restrict__ xT,
+                                                 float *__restrict__ g, float *__restrict__ gT,
+                                                 double *__restrict__ kl_part, int mode) {
+  if (subset_dev) subset = *subset_dev;
+  const LorIdx id = lor_index(P, subset, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+  double kl = 0.0;
+  if (id.ok) {
+    Lor L;
+    lor_setup(P, id.v, id.p, id.r, L);
+    const int T = tof_bins<TT>(P);
+    const size_t lor = ((size_t)id.v * P.nplane + id.p) * P.nrad + id.r;
+    const float m = __ldg(&P.m[lor]);
+    float acc[TT];
+    if (mode != MODE_SENS) forward_lor<TT>(P, L, L.xdrive ? xT : x, acc);
+    float q[TT];
+    bool any = false;
+    const float mL = m * L.L;
+#pragma unroll
+    for (int b = 0; b < TT; ++b) {
+      q[b] = 0.f;
+      if (b < T) {
+        if (mode == MODE_SENS) {
+          q[b] = mL;
+        } else {
+          const size_t bi = lor * T + b;
+          const float ybar = fmaf(mL, acc[b], __ldg(&P.r[bi]));
+          const float yb = load_y(P, bi);
+          if (!(ybar > 0.f)) {
+            if (yb > 0.f) atomicOr(P.err, 1);
+            q[b] = (mode == MODE_GRAD && yb == 0.f) ? mL : 0.f;
+            if (kl_part && yb == 0.f) kl += (double)fmaxf(ybar, 0.f);
+          } else {
+            if (mode == MODE_GRAD) q[b] = mL * (1.f - yb / ybar);
+            else if (mode == MODE_EM) q[b] = mL * (yb / ybar);
+            if (kl_part) {
+              const double db = ybar, dy = yb;
+              kl += (yb > 0.f) ? (db - dy + dy * log(dy / db)) : db;
+            }
+          }
+        }
+        any |= q[b] != 0.f;
+      }
+    }
+    if (mode != MODE_OBJ && any) back_lor<TT>(P, L, L.xdrive ? gT : g, q);
+  }
+  if (kl_part) block_sum_store(kl, kl_part + blockIdx.x);
+}
+
+// m = sens * exp(-P mu) for every LOR (non-TOF forward of the attenuation image).
+__global__ void __launch_bounds__(kBlock) k_mult(DevPlan P, const float *__restrict__ mu,
+                                                 const float *__restrict__ muT,
+                                                 const float *__restrict__ sens, float *__restrict__ m) {
+  const LorIdx id = lor_index(P, -1, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+  if (!id.ok) return;
+  float s = sens ? __ldg(&sens[id.l]) : 1.f;
+  if (mu) {
+    Lor L;
+    lor_setup(P, id.v, id.p, id.r, L);
+    float acc[1];
+    forward_lor<1>(P, L, L.xdrive ? muT : mu, acc);
+    s *= expf(-acc[0] * L.L);
+  }
+  m[id.l] = s;
+}
+
+// Tiled transpose of each z-slice: src [z][A][B] -> dst [z][B][A].  accumulate: 0 writes,
+// 1 adds, 2 adds and clears the source tile (keeps an accumulator zeroed between uses).
+__global__ void k_transpose(float *__restrict__ src, float *__restrict__ dst, int A, int B,
+                            int accumulate) {
+  __shared__ float tile[32][33];
+  const int z = blockIdx.z;
+  const int b0 = blockIdx.x * 32, a0 = blockIdx.y * 32;
+  const size_t off = (size_t)z * A * B;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int a = a0 + j, b = b0 + threadIdx.x;
+    if (a < A && b < B) {
+      tile[j][threadIdx.x] = src[off + (size_t)a * B + b];
+      if (accumulate == 2) src[off + (size_t)a * B + b] = 0.f;
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int b = b0 + j, a = a0 + threadIdx.x;
+    if (a < A && b < B) {
+      const size_t o = off + (size_t)b * A + a;
+      dst[o] = accumulate ? dst[o] + tile[threadIdx.x][j] : tile[threadIdx.x][j];
+    }
+  }
+}
+
+// Voxel-driven deterministic backprojection: each thread gathers, in a fixed order
+// with compensated summation, every (LOR, sample) whose bilinear footprint covers its
+// voxel.  The sample positions are computed with exactly the arithmetic of
+// lor_setup/sample_at, so the weights are those of the ray-driven pair.  ones != 0
+// backprojects q = 1 (sensitivity A^T 1).
+template <int TT>
+__global__ void __launch_bounds__(kBlock) k_back_det(DevPlan P, DevPlanDet D, int subset,
+                                                     const float *__restrict__ q, float *__restrict__ g,
+                                                     int ones) {
+  const int nvox = P.nx * P.ny * P.nz;
+  const int vox = blockIdx.x * blockDim.x + threadIdx.x;
+  if (vox >= nvox) return;
+  const int ix = vox % P.nx, iy = (vox / P.nx) % P.ny, iz = vox / (P.nx * P.ny);
+  const int nsub = subset < 0 ? 1 : P.nsub;
+  const int s0 = subset < 0 ? 0 : subset;
+  const int T = tof_bins<TT>(P);
+  const float du = P.tof_w * P.tof_inv;
+  float sum = 0.f, cmp = 0.f;
+  int jv = 0;
+  for (int v = s0; v < P.nview; v += nsub, ++jv) {
+    const float4 vw = __ldg(&P.view[v]);
+    const bool xd = vw.x != 0.f;
+    const int i = xd ? ix : iy, j = xd ? iy : ix;
+    const float dfb = vw.y, dau = vw.z;
+    const float2 aff = __ldg(&D.view_aff[v]);
+    const float base = fmaf((float)i, dfb, aff.x);
+    const float ra = ((float)(j - 1) - base) / aff.y, rb = ((float)(j + 1) - base) / aff.y;
+    const int r0 = max(0, (int)floorf(fmaxf(fminf(ra, rb), -4.f)) - 1);
+    const int r1 = min(P.nrad - 1, (int)ceilf(fminf(fmaxf(ra, rb), (float)P.nrad + 4.f)) + 1);
+    for (int r = r0; r <= r1; ++r) {
+      const float4 vr = __ldg(&P.vr[v * P.nrad + r]);
+      const float fb = fmaf((float)i, dfb, vr.x);
+      const float fbf = floorf(fb);
+      const int ib = (int)fbf;
+      const float wb = fb - fbf;
+      float wbj;
+      if (ib == j) wbj = 1.f - wb;
+      else if (ib + 1 == j) wbj = wb;
+      else continue;
+      const float t0b = vr.y, inv2h = vr.z;
+      const float g1 = dau * inv2h, g2 = t0b * inv2h;
+      for (int p = 0; p < P.nplane; ++p) {
+        const float4 pl = __ldg(&P.plane[p]);
+        const float dfz = g1 * pl.y;
+        const float fz0 = fmaf(g2, pl.y, pl.x);
+        const float fz = fmaf((float)i, dfz, fz0);
+        const float fzf = floorf(fz);
+        const int jz = (int)fzf;
+        const float wz = fz - fzf;
+        float wzk;
+        if (jz == iz) wzk = 1.f - wz;
+        else if (jz + 1 == iz) wzk = wz;
+        else continue;
+        const float kk = pl.z * inv2h;
+        const float sec = sqrtf(fmaf(kk, kk, 1.f));
+        const float mL = __ldg(&P.m[((size_t)v * P.nplane + p) * P.nrad + r]) * (fabsf(dau) * sec);
+        const size_t ql = (((size_t)jv * P.nplane + p) * P.nrad + r) * T;
+        float val;
+        if (TT == 1) {
+          val = ones ? 1.f : __ldg(&q[ql]);
+        } else {
+          const float t = fmaf((float)i, dau * sec, t0b * sec);
+          const float u0 = (P.tof_e0 - t) * P.tof_inv;
+          float uprev = u0, Gprev = tof_edge_G(P, u0);
+          val = 0.f;
+#pragma unroll
+          for (int k = 1; k <= TT; ++k) {
+            if (k <= T) {
+              const float u = fmaf((float)k, du, u0);
+              const float G = tof_edge_G(P, u);
+              const float qb = ones ? 1.f : __ldg(&q[ql + k - 1]);
+              val = fmaf(qb, tof_bin_weight(P, uprev, Gprev, u, G), val);
+              uprev = u;
+              Gprev = G;
+            }
+          }
+        }
+        kahan_add(sum, cmp, mL * val * (wbj * wzk));
+      }
+    }
+  }
+  g[vox] = sum;
+}
+
+// KL ratio on a compact subset sinogram holding A_s x: mode MODE_GRAD writes
+// 1 - y/ybar, MODE_EM y/ybar; optional FP64 KL partial sums per block.
+__global__ void __launch_bounds__(kBlock) k_ratio(DevPlan P, int subset, const float *__restrict__ ax,
+                                                  float *__restrict__ q, double *__restrict__ kl_part,
+                                                  int mode) {
+  const int T = P.T > 1 ? P.T : 1;
+  const long long bin = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const LorIdx id = lor_index(P, subset, bin / T);
+  double kl = 0.0;
+  if (id.ok) {
+    const int b = (int)(bin % T);
+    const size_t bi = (((size_t)id.v * P.nplane + id.p) * P.nrad + id.r) * T + b;
+    const float ybar = ax[bin] + __ldg(&P.r[bi]);
+    const float yb = load_y(P, bi);
+    float qq;
+    if (!(ybar > 0.f)) {
+      if (yb > 0.f) atomicOr(P.err, 1);
+      qq = (mode == MODE_GRAD && yb == 0.f) ? 1.f : 0.f;
+      if (yb == 0.f) kl = (double)fmaxf(ybar, 0.f);
+    } else {
+      qq = mode == MODE_GRAD ? 1.f - yb / ybar : yb / ybar;
+      const double db = ybar, dy = yb;
+      kl = (yb > 0.f) ? (db - dy + dy * log(dy / db)) : db;
+    }
+    if (q) q[bin] = qq;
+  }
+  if (kl_part) block_sum_store(kl, kl_part + blockIdx.x);
+}
+
+// ----------------------------------------------------------------- launchers
+static int views_in(const DevPlan &P, int subset) {
+  if (subset < 0) return P.nview;
+  return (P.nview - subset + P.nsub - 1) / P.nsub;
+}
+
+static unsigned blocks_for(const DevPlan &P, int nviews) {
+  const long long n = (long long)nviews * P.nplane * P.nrad;
+  return (unsigned)((n + kBlock - 1) / kBlock);
+}
+
+int grad_blocks(const DevPlan &P, int max_views) { return (int)blocks_for(P, max_views); }
+
+#define PET_TOF_DISPATCH(KERNEL, GRID, STREAM, ...)                             \
+  do {                                                                         \
+    if (P.T <= 1) KERNEL<1><<<GRID, kBlock, 0, STREAM>>>(__VA_ARGS__);         \
+    else if (P.T == 11) KERNEL<11><<<GRID, kBlock, 0, STREAM>>>(__VA_ARGS__);  \
+    else if (P.T == 13) KERNEL<13><<<GRID, kBlock, 0, STREAM>>>(__VA_ARGS__);  \
+    else if (P.T <= 16) KERNEL<16><<<GRID, kBlock, 0, STREAM>>>(__VA_ARGS__);  \
+    else KERNEL<32><<<GRID, kBlock, 0, STREAM>>>(__VA_ARGS__);                 \
+  } while (0)
+
+cudaError_t launch_forward(const DevPlan &P, int subset, const float *x, const float *xT,
+                           float *out, cudaStream_t st) {
+  const unsigned grid = blocks_for(P, views_in(P, subset));
+  if (grid == 0) return cudaSuccess;
+  PET_TOF_DISPATCH(k_forward, grid, st, P, subset, x, xT, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_back(const DevPlan &P, int subset, const float *q, float *g, float *gT,
+                        cudaStream_t st) {
+  const unsigned grid = blocks_for(P, views_in(P, subset));
+  if (grid == 0) return cudaSuccess;
+  PET_TOF_DISPATCH(k_back, grid, st, P, subset, q, g, gT);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad(const DevPlan &P, int subset, const int *subset_dev, const float *x,
+                        const float *xT, float *g, float *gT, double *kl_part, int mode,
+                        int *nblocks_out, cudaStream_t st) {
+  // with a device-side subset index the grid covers the largest subset
+  const int nv = subset_dev ? (P.nview + P.nsub - 1) / P.nsub : views_in(P, subset);
+  const unsigned grid = blocks_for(P, nv);
+  if (nblocks_out) *nblocks_out = (int)grid;
+  if (grid == 0) return cudaSuccess;
+  PET_TOF_DISPATCH(k_grad, grid, st, P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_back_det(const DevPlan &P, const DevPlanDet &D, int subset, const float *q,
+                            float *g, int ones, cudaStream_t st) {
+  const long long nvox = (long long)P.nx * P.ny * P.nz;
+  const unsigned grid = (unsigned)((nvox + kBlock - 1) / kBlock);
+  PET_TOF_DISPATCH(k_back_det, grid, st, P, D, subset, q, g, ones);
+  return cudaGetLastError();
+}
+
+int ratio_blocks(const DevPlan &P, int subset) {
+  const long long n = (long long)views_in(P, subset) * P.nplane * P.nrad * (P.T > 1 ? P.T : 1);
+  return (int)((n + kBlock - 1) / kBlock);
+}
+
+cudaError_t launch_ratio(const DevPlan &P, int subset, const float *ax, float *q, double *kl_part,
+                         int mode, cudaStream_t st) {
+  const int grid = ratio_blocks(P, subset);
+  if (grid == 0) return cudaSuccess;
+  k_ratio<<<grid, kBlock, 0, st>>>(P, subset, ax, q, kl_part, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mult(const DevPlan &P, const float *mu, const float *muT, const float *sens,
+                        float *m, cudaStream_t st) {
+  const unsigned grid = blocks_for(P, P.nview);
+  k_mult<<<grid, kBlock, 0, st>>>(P, mu, muT, sens, m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(const float *src, float *dst, int nx, int ny, int nz, int to_xfast,
+                             int accumulate, cudaStream_t st) {
+  // to_xfast = 0: x[z][y][x] -> xT[z][x][y]  (A = ny, B = nx)
+  // to_xfast = 1: xT[z][x][y] -> x[z][y][x]  (A = nx, B = ny)
+  const int A = to_xfast ? nx : ny, B = to_xfast ? ny : nx;
+  dim3 grid((B + 31) / 32, (A + 31) / 32, nz), block(32, 8);
+  k_transpose<<<grid, block, 0, st>>>(const_cast<float *>(src), dst, A, B, accumulate);
+  return cudaGetLastError();
+}
+
+}  // namespace petgb
