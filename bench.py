@@ -1,0 +1,370 @@
+"""Benchmark of the subset-gradient path on the 3D non-TOF brain workload.
+
+Workload (config "c2"): 128x128x47 image (2x2x2.8 mm), cylindrical scanner sinogram 250
+radial x 168 views x 109 planes, seeded brain-like phantom, 1e7 counts, 20% smooth
+background, 21 view subsets.  One STEP is one SVRG outer loop of Algorithm 1: the
+harmonic preconditioner update (eq. 8), a snapshot refresh (21 subset gradients) and
+41 inner iterations (eq. 9 + eq. 6), i.e. 62 subset gradients (forward projection,
+KL ratio, backprojection and RDP gradient) per step.
+
+Metric: subset gradients per second (whole job: all ranks).  Multi-GPU runs are
+independent replicas (one reconstruction per rank, no collective on the data path).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "subset grads/s (fwd+back+RDP) & % HBM roofline; time to 1% NRMSE vs oracle"
+UNIT = "subset_grads/s"
+WORKLOAD = ("c2: 3D non-TOF 128x128x47 (2x2x2.8 mm), sinogram 250 radial x 168 views x 109 planes "
+            "(span-3 segments 0 and +-9), 1e7 counts, 21 subsets, SVRG + harmonic preconditioner")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--mode", default="step", choices=["step", "grad"],
+                    help="grad: only the fused subset-gradient op, for profiler captures")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("proj_kernels.cu", "pet_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2506_04976_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_tag):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if
+    the kernel source is unchanged since the counters were taken; else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    if d.get("source_hash") != source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, out):
+        self.out = out
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.out, "w")
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.p or not os.path.exists(self.out):
+            return None
+        rows = []
+        for line in open(self.out):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), util=float(parts[4]),
+                                 hw=parts[6], hwt=parts[7], swt=parts[8], pcap=parts[9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        load = [r for r in rows if r["util"] >= 50] or rows
+        reasons = []
+        for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                          ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+            if any(r[key].lower() == "active" for r in load):
+                reasons.append(name)
+        return {"sm_mhz": float(np.median([r["sm"] for r in load])),
+                "sm_max_mhz": max(r["smax"] for r in load), "reasons": reasons,
+                "samples": len(load)}
+
+
+def make_inputs(seed):
+    from paper_2506_04976_gb300 import synth
+    return synth.make_problem("c2", seed)
+
+
+def algorithmic_bytes_per_grad(p):
+    """Fused subset gradient: counts (u16) + background (f32) + factors m (f32) per LOR of
+    one subset, one read of the image and one write of the gradient (f32)."""
+    g = p["geom"]
+    n = p["nsub"]
+    lors = (g["nview"] // n) * len(g["z1"]) * g["nrad"]
+    N = g["nx"] * g["ny"] * g["nz"]
+    return lors * (p["y"].itemsize + 4 + 4) + 2 * 4 * N
+
+
+def cpu_baseline(p, seconds, steps=None):
+    """The FP64 oracle, single-threaded, on whole subset gradients of the same workload
+    (data gradient of one subset + RDP gradient), repeated for about `seconds`."""
+    import oracle as O
+    G = O.Geometry(p["geom"])
+    m = O.multiplicative(G, p["mu"], p["sens"])
+    x = np.maximum(p["x_true"], 0.05 * p["x_true"].max())
+    sp = (p["geom"]["dx"], p["geom"]["dy"], p["geom"]["dz"])
+    times = []
+    s = 0
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        O.data_grad(G, p["nsub"], s % p["nsub"], x, m, p["r"], p["y"])
+        O.rdp(x, sp, p["gamma"], p["eps"])
+        times.append(time.perf_counter() - t0)
+        s += 1
+        if steps is not None:
+            if s >= steps:
+                break
+        elif time.perf_counter() - t_start >= seconds:
+            break
+    return times
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    p = make_inputs(0)
+    # warm-up and timed steps: each step is one whole subset gradient in the oracle
+    cpu_baseline(p, 0, steps=args.warmup) if args.warmup > 0 else None
+    times = cpu_baseline(p, 0, steps=args.steps)
+    total = sum(times)
+    value = len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "step": "one subset gradient"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{len(times)} full-size subset gradients (fwd+back+RDP), FP64, 1 thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_grad_only(args, pet, dev):
+    """Subset gradients only (objective_grad on successive subsets), for ncu captures."""
+    import torch
+    p = make_inputs(0)
+    plan = pet.Plan(p["geom"], p["nsub"])
+    plan.set_data(torch.from_numpy(p["y"].view(np.int16)).to(dev), torch.from_numpy(p["r"]).to(dev),
+                  torch.from_numpy(p["mu"].astype(np.float32)).to(dev),
+                  torch.from_numpy(p["sens"].astype(np.float32)).to(dev))
+    x = torch.from_numpy(np.maximum(p["x_true"], 0.05 * p["x_true"].max()).astype(np.float32)).to(dev)
+    gbuf = torch.empty_like(x)
+    for i in range(args.warmup):
+        plan.objective_grad(x, i % p["nsub"], g=gbuf, want_obj=False)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for i in range(args.steps):
+        plan.objective_grad(x, i % p["nsub"], g=gbuf, want_obj=False)
+    b.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "grad", "ms_per_call": a.elapsed_time(b) / max(args.steps, 1)}))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    from paper_2506_04976_gb300 import binding as pet
+
+    if args.mode == "grad":
+        return run_grad_only(args, pet, dev)
+    p = make_inputs(rank)
+    g = p["geom"]
+    n = p["nsub"]
+    step_len = 2 * n                      # one SVRG outer loop (omega = 2)
+    grads_per_step = 3 * n - 1            # n at the refresh + (2n - 1) inner iterations
+    plan = pet.Plan(g, n)
+    y_host = torch.from_numpy(p["y"].view(np.int16)).pin_memory()
+    r_host = torch.from_numpy(p["r"]).pin_memory()
+    y = y_host.to(dev)
+    r = r_host.to(dev)
+    plan.set_data(y, r, torch.from_numpy(p["mu"].astype(np.float32)).to(dev),
+                  torch.from_numpy(p["sens"].astype(np.float32)).to(dev))
+    # one OSEM epoch from a uniform image (Sec. 3.1 initialisation)
+    x0 = torch.ones(plan.img_shape, device=dev)
+    for s in range(n):
+        plan.em_update(x0, s)
+    x0_host = x0.cpu().pin_memory()
+    total_steps = args.warmup + args.steps + (0 if args.no_e2e else args.steps)
+    pcs = [k * step_len for k in range(total_steps + 1)]
+    solver = pet.Solver(plan, algo=pet.SVRG, omega=2, step_rule=pet.STEP_VANISH, tau0=1.0, eta=0.02,
+                        precond_kind=1, alpha=1.0, delta_rel=1e-6, pc_iters=pcs, beta=p["beta"],
+                        gamma=p["gamma"], eps=p["eps"], seed=1234 + rank, use_graph=True)
+    solver.set_image(x0)
+    solver.profile(True)
+    flush = torch.empty(64 * 1024 * 1024, device=dev)  # 256 MB > L2 (129 MB)
+
+    for _ in range(args.warmup):
+        solver.run(step_len)
+    torch.cuda.synchronize()
+    solver.kernel_time()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kern_ms, kern_n = 0.0, 0
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    clk = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv"))
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    launches0 = pet.launch_count()
+    wall0 = time.perf_counter()
+    with clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record()
+            solver.run(step_len)
+            ev[i][1].record()
+            torch.cuda.synchronize()
+            ms, nl = solver.kernel_time()
+            kern_ms += ms
+            kern_n += nl
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = pet.launch_count() - launches0
+    if pg:
+        pg.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = sum(step_ms) / 1e3
+    if pg:
+        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        t_total = float(tt)
+    units = grads_per_step * args.steps * world
+    value = units / t_total
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        x_dev = torch.empty_like(x0)
+        xo = torch.empty(plan.img_shape, pin_memory=True)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            y.copy_(y_host, non_blocking=True)
+            r.copy_(r_host, non_blocking=True)
+            x_dev.copy_(x0_host, non_blocking=True)
+            solver.set_image(x_dev)
+            solver.run(step_len)
+            xo.copy_(solver.image(), non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        te = a.elapsed_time(b) / 1e3
+        if pg:
+            tt = torch.tensor([te], device=dev, dtype=torch.float64)
+            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+            te = float(tt)
+        e2e = {"value": grads_per_step * args.steps * world / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(y_host.numel() * 2 + r_host.numel() * 4 + x0_host.numel() * 4),
+               "d2h_bytes_per_step": int(xo.numel() * 4)}
+        solver.kernel_time()
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+
+    peak, peak_kind = measured_peaks()
+    kavg = kern_ms / max(kern_n, 1)
+    abytes = algorithmic_bytes_per_grad(p)
+    achieved = abytes / (kavg * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": ncu_traffic("k_grad_c2"),
+                "kernel": "k_grad<1> (fused forward, KL ratio, backprojection of one subset)",
+                "kernel_ms": kavg, "launches_timed": kern_n, "algorithmic_bytes": abytes,
+                "peak_kind": f"hbm_gbs {peak_kind}"}
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        times = cpu_baseline(p, args.cpu_seconds)
+        cpu = {"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{len(times)} full-size c2 subset gradients (fwd+back+RDP), FP64, 1 thread"}
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "step": "SVRG outer loop: precond update + refresh + 41 inner "
+                   "iterations = 62 subset gradients", "l2": "flushed between steps (256 MB write)",
+                   "graph": "one CUDA graph per epoch", "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks, "wall_s_timed": wall,
+    }
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -198,6 +198,19 @@ pet_status pet_solver_run(pet_solver *s, long long niter, void *stream);
 long long pet_solver_taus(const pet_solver *s, double *taus, long long cap);
 long long pet_solver_iteration(const pet_solver *s);
 
+/* Event timing of the fused subset-gradient kernel launched by the solver (the
+ * dominant kernel of an iteration), recorded on the launching stream and inside
+ * captured graphs.  Slots are unique within one SVRG outer loop (omega*n iterations)
+ * or one SGD/SAGA epoch, so read the time at least once per outer loop / epoch.
+ * pet_solver_kernel_time synchronises on the recorded events, returns the summed
+ * duration (ms) and the number of launches since the previous call, and resets. */
+pet_status pet_solver_profile(pet_solver *s, int enable);
+pet_status pet_solver_kernel_time(pet_solver *s, double *total_ms, long long *launches);
+
+/* Number of kernels this library has launched in the process so far (a replayed
+ * epoch graph counts its kernel nodes). */
+long long pet_launch_count(void);
+
 const char *pet_status_str(pet_status st);
 
 #ifdef __cplusplus

@@ -99,6 +99,9 @@ _sigs = {
     "pet_solver_run": (C.c_int, [_vp, C.c_longlong, _vp]),
     "pet_solver_taus": (C.c_longlong, [_vp, C.POINTER(C.c_double), C.c_longlong]),
     "pet_solver_iteration": (C.c_longlong, [_vp]),
+    "pet_solver_profile": (C.c_int, [_vp, C.c_int]),
+    "pet_launch_count": (C.c_longlong, []),
+    "pet_solver_kernel_time": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -245,6 +248,11 @@ class Plan:
         return out
 
 
+def launch_count():
+    """Kernels launched by the library so far (graph replays count their kernel nodes)."""
+    return _lib.pet_launch_count()
+
+
 def _wrap(ptr, shape):
     """Device buffer owned by the library -> a torch view (no copy, no ownership)."""
     if not ptr:
@@ -318,6 +326,15 @@ class Solver:
     @property
     def k(self):
         return _lib.pet_solver_iteration(self._h)
+
+    def profile(self, enable=True):
+        _ck(_lib.pet_solver_profile(self._h, int(bool(enable))), "pet_solver_profile")
+
+    def kernel_time(self):
+        """(total ms, launches) of the fused subset-gradient kernel since the last call."""
+        ms, n = C.c_double(), C.c_longlong()
+        _ck(_lib.pet_solver_kernel_time(self._h, C.byref(ms), C.byref(n)), "pet_solver_kernel_time")
+        return ms.value, n.value
 
     def taus(self):
         torch.cuda.current_stream().synchronize()

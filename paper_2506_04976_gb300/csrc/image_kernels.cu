@@ -45,7 +45,7 @@ __device__ __forceinline__ double block_sum_d(double v) {
   return s;  // valid in thread 0
 }
 
-template <bool KAPPA>
+template <bool KAPPA, bool VAL>
 __global__ void __launch_bounds__(RDP_TX * RDP_TY) k_rdp(RdpArgs a, const float *__restrict__ x,
                                                           float *__restrict__ grad, float *__restrict__ hdiag,
                                                           double *__restrict__ val_part, int accumulate) {
@@ -111,18 +111,18 @@ __global__ void __launch_bounds__(RDP_TX * RDP_TY) k_rdp(RdpArgs a, const float 
             gsum = fmaf(w * d * ((2.f * phi - d) - a.gamma * ad), inv2, gsum);
             const float e2 = fmaf(2.f, xj, a.eps);
             hsum = fmaf(2.f * w * e2 * e2, inv2 * inv, hsum);
-            vs = fmaf(w * d * d, inv, vs);
+            if (VAL) vs = fmaf(w * d * d, inv, vs);
           }
         }
       }
       const size_t gi = (size_t)z * nxy + (size_t)gy * a.nx + gx;
       if (grad) grad[gi] = accumulate ? fmaf(a.scale, gsum, grad[gi]) : a.scale * gsum;
       if (hdiag) hdiag[gi] = a.scale * hsum;
-      vsum += 0.5 * (double)vs;
+      if (VAL) vsum += 0.5 * (double)vs;
     }
     __syncthreads();
   }
-  if (val_part) {
+  if (VAL) {
     const double s = block_sum_d(vsum * (double)a.scale);
     if (tid == 0) val_part[blockIdx.x] = s;
   }
@@ -133,8 +133,14 @@ cudaError_t launch_rdp(const RdpArgs &a, const float *x, float *grad, float *hdi
   const int nb = rdp_blocks(a.nx, a.ny, a.nz);
   if (nblocks_out) *nblocks_out = nb;
   dim3 block(RDP_TX, RDP_TY);
-  if (a.kappa) k_rdp<true><<<nb, block, 0, st>>>(a, x, grad, hdiag, val_part, accumulate);
-  else k_rdp<false><<<nb, block, 0, st>>>(a, x, grad, hdiag, val_part, accumulate);
+  note_launch();
+  if (a.kappa) {
+    if (val_part) k_rdp<true, true><<<nb, block, 0, st>>>(a, x, grad, hdiag, val_part, accumulate);
+    else k_rdp<true, false><<<nb, block, 0, st>>>(a, x, grad, hdiag, val_part, accumulate);
+  } else {
+    if (val_part) k_rdp<false, true><<<nb, block, 0, st>>>(a, x, grad, hdiag, val_part, accumulate);
+    else k_rdp<false, false><<<nb, block, 0, st>>>(a, x, grad, hdiag, val_part, accumulate);
+  }
   return cudaGetLastError();
 }
 
@@ -154,6 +160,7 @@ __global__ void k_reduce_sum(const double *__restrict__ part, int n, double *out
 
 cudaError_t launch_reduce_sum(const double *part, int n, double *out, int accumulate,
                               cudaStream_t st) {
+  note_launch();
   k_reduce_sum<<<1, 1024, 0, st>>>(part, n, out, accumulate);
   return cudaGetLastError();
 }
@@ -189,7 +196,9 @@ __global__ void k_max_final(const float *part, int n, float *out) {
 
 cudaError_t launch_max(const float *x, size_t n, float *part, float *out, cudaStream_t st) {
   const int nb = max_blocks(n);
+  note_launch();
   k_max_part<<<nb, 256, 0, st>>>(x, n, part);
+  note_launch();
   k_max_final<<<1, 1024, 0, st>>>(part, nb, out);
   return cudaGetLastError();
 }
@@ -212,6 +221,7 @@ static unsigned grid_1d(size_t n) { return (unsigned)min((size_t)152 * 16, (n + 
 cudaError_t launch_precond(const float *x, const float *sens, const float *hdiag, float alpha,
                            const float *xmax, float delta_rel, float *D, size_t n,
                            cudaStream_t st) {
+  note_launch();
   k_precond<<<grid_1d(n), 256, 0, st>>>(x, sens, hdiag, alpha, xmax, delta_rel, D, n);
   return cudaGetLastError();
 }
@@ -226,6 +236,7 @@ __global__ void k_em_apply(float *__restrict__ x, const float *__restrict__ bp,
 
 cudaError_t launch_em_apply(float *x, const float *bp, const float *sens, size_t n,
                             cudaStream_t st) {
+  note_launch();
   k_em_apply<<<grid_1d(n), 256, 0, st>>>(x, bp, sens, n);
   return cudaGetLastError();
 }
@@ -259,7 +270,9 @@ __global__ void k_nrmse_final(const double *part, int nb, double *out) {
 cudaError_t launch_nrmse(const float *x, const float *ref, const uint8_t *mask, const uint8_t *bg,
                          size_t n, double *part, double *out, cudaStream_t st) {
   const int nb = nrmse_blocks(n);
+  note_launch();
   k_nrmse_part<<<nb, 256, 0, st>>>(x, ref, mask, bg, n, part);
+  note_launch();
   k_nrmse_final<<<1, 32, 0, st>>>(part, nb, out);
   return cudaGetLastError();
 }

@@ -94,6 +94,18 @@ __device__ __forceinline__ void lor_setup(const DevPlan &P, int v, int p, int r,
   L.i1 = min(Na - 1, (int)ceilf(hi) + 1);
 }
 
+// Makes the sample range uniform across the warp (union of the lanes' ranges) so that
+// at every step all lanes sample the same driving plane and touch adjacent voxels.
+// Samples outside a lane's own range fall outside the image and carry zero weight, so
+// the sums are unchanged.  Every lane of the warp must call this.
+__device__ __forceinline__ void warp_uniform_range(Lor &L, bool valid) {
+  const bool own = valid && L.i0 <= L.i1;
+  const int lo = __reduce_min_sync(0xffffffffu, own ? L.i0 : 0x7fffffff);
+  const int hi = __reduce_max_sync(0xffffffffu, own ? L.i1 : -1);
+  L.i0 = lo;
+  L.i1 = hi;
+}
+
 // Bilinear sample position at plane i.
 struct Samp {
   int base;       // frame index of neighbour (iz, i, ib)
@@ -140,6 +152,11 @@ __device__ __forceinline__ float load_y(const DevPlan &P, size_t idx) {
 }
 
 // ----------------------------------------------------------------- launchers
+// Count of kernel launches enqueued by this library (graph replays add the number of
+// kernel nodes of the replayed graph).
+void note_launch(long long n = 1);
+long long launch_count();
+
 // Projector kernels (proj_kernels.cu).  `subset` < 0 means all views.
 enum GradMode { MODE_GRAD = 0, MODE_EM = 1, MODE_OBJ = 2, MODE_SENS = 3 };
 

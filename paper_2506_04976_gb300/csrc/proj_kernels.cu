@@ -4,9 +4,15 @@
 // sensitivity).  One thread owns one LOR; adjacent threads own adjacent radial bins of
 // the same view and plane, so their samples at a given plane touch adjacent voxels of
 // the driving-frame image.
+#include <atomic>
+
 #include "pet_internal.cuh"
 
 namespace petgb {
+
+static std::atomic<long long> g_launches{0};
+void note_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // ----------------------------------------------------------------- helpers
 __device__ __forceinline__ void kahan_add(float &sum, float &c, float v) {
@@ -42,7 +48,8 @@ __device__ __forceinline__ int tof_bins(const DevPlan &P) {
 // length L is applied by the caller.
 template <int TT>
 __device__ __forceinline__ void forward_lor(const DevPlan &P, const Lor &L,
-                                            const float *__restrict__ img, float (&acc)[TT]) {
+                                            const float *__restrict__ img, float (&acc)[TT],
+                                            bool act = true) {
   const int Na = L.xdrive ? P.nx : P.ny;
   const int Nb = L.xdrive ? P.ny : P.nx;
   const int plane = Na * Nb;
@@ -52,6 +59,7 @@ __device__ __forceinline__ void forward_lor(const DevPlan &P, const Lor &L,
   for (int b = 0; b < TT; ++b) { acc[b] = 0.f; cmp[b] = 0.f; }
   const float du = P.tof_w * P.tof_inv;
   for (int i = L.i0; i <= L.i1; ++i) {
+    if (!act || i >= Na) continue;
     Samp S;
     sample_at(L, i, Na, Nb, P.nz, S);
     const float val = bilinear(img, S, plane);
@@ -79,13 +87,14 @@ __device__ __forceinline__ void forward_lor(const DevPlan &P, const Lor &L,
 // Back: scatter sum_b q[b] w_b(t) * bilinear weights; q already includes m and L.
 template <int TT>
 __device__ __forceinline__ void back_lor(const DevPlan &P, const Lor &L, float *__restrict__ img,
-                                         const float (&q)[TT]) {
+                                         const float (&q)[TT], bool act = true) {
   const int Na = L.xdrive ? P.nx : P.ny;
   const int Nb = L.xdrive ? P.ny : P.nx;
   const int plane = Na * Nb;
   const int T = tof_bins<TT>(P);
   const float du = P.tof_w * P.tof_inv;
   for (int i = L.i0; i <= L.i1; ++i) {
+    if (!act || i >= Na) continue;
     Samp S;
     sample_at(L, i, Na, Nb, P.nz, S);
     float val;
@@ -138,11 +147,12 @@ template <int TT>
 __global__ void __launch_bounds__(kBlock) k_forward(DevPlan P, int subset, const float *__restrict__ x,
                                                     const float *__restrict__ xT, float *__restrict__ out) {
   const LorIdx id = lor_index(P, subset, (long long)blockIdx.x * blockDim.x + threadIdx.x);
-  if (!id.ok) return;
-  Lor L;
-  lor_setup(P, id.v, id.p, id.r, L);
+  Lor L = {};
+  if (id.ok) lor_setup(P, id.v, id.p, id.r, L);
+  warp_uniform_range(L, id.ok);
   float acc[TT];
-  forward_lor<TT>(P, L, L.xdrive ? xT : x, acc);
+  forward_lor<TT>(P, L, L.xdrive ? xT : x, acc, id.ok);
+  if (!id.ok) return;
   const int T = tof_bins<TT>(P);
   const float m = __ldg(&P.m[((size_t)id.v * P.nplane + id.p) * P.nrad + id.r]) * L.L;
 #pragma unroll
@@ -154,19 +164,21 @@ template <int TT>
 __global__ void __launch_bounds__(kBlock) k_back(DevPlan P, int subset, const float *__restrict__ q,
                                                  float *__restrict__ g, float *__restrict__ gT) {
   const LorIdx id = lor_index(P, subset, (long long)blockIdx.x * blockDim.x + threadIdx.x);
-  if (!id.ok) return;
-  Lor L;
-  lor_setup(P, id.v, id.p, id.r, L);
+  Lor L = {};
+  if (id.ok) lor_setup(P, id.v, id.p, id.r, L);
+  warp_uniform_range(L, id.ok);
   const int T = tof_bins<TT>(P);
-  const float m = __ldg(&P.m[((size_t)id.v * P.nplane + id.p) * P.nrad + id.r]) * L.L;
   float qq[TT];
   bool any = false;
+  if (id.ok) {
+    const float m = __ldg(&P.m[((size_t)id.v * P.nplane + id.p) * P.nrad + id.r]) * L.L;
 #pragma unroll
-  for (int b = 0; b < TT; ++b) {
-    qq[b] = b < T ? __ldg(&q[(size_t)id.l * T + b]) * m : 0.f;
-    any |= qq[b] != 0.f;
+    for (int b = 0; b < TT; ++b) {
+      qq[b] = b < T ? __ldg(&q[(size_t)id.l * T + b]) * m : 0.f;
+      any |= qq[b] != 0.f;
+    }
   }
-  if (any) back_lor<TT>(P, L, L.xdrive ? gT : g, qq);
+  back_lor<TT>(P, L, L.xdrive ? gT : g, qq, any);
 }
 
 __device__ __forceinline__ void block_sum_store(double v, double *out) {
@@ -193,21 +205,21 @@ __global__ void __launch_bounds__(kBlock) k_grad(DevPlan P, int subset, const in
   if (subset_dev) subset = *subset_dev;
   const LorIdx id = lor_index(P, subset, (long long)blockIdx.x * blockDim.x + threadIdx.x);
   double kl = 0.0;
-  if (id.ok) {
-    Lor L;
-    lor_setup(P, id.v, id.p, id.r, L);
+  Lor L = {};
+  if (id.ok) lor_setup(P, id.v, id.p, id.r, L);
+  warp_uniform_range(L, id.ok);
+  float acc[TT];
+  if (mode != MODE_SENS) forward_lor<TT>(P, L, L.xdrive ? xT : x, acc, id.ok);
+  float q[TT];
+  bool any = false;
+  {
     const int T = tof_bins<TT>(P);
-    const size_t lor = ((size_t)id.v * P.nplane + id.p) * P.nrad + id.r;
-    const float m = __ldg(&P.m[lor]);
-    float acc[TT];
-    if (mode != MODE_SENS) forward_lor<TT>(P, L, L.xdrive ? xT : x, acc);
-    float q[TT];
-    bool any = false;
-    const float mL = m * L.L;
+    const size_t lor = id.ok ? ((size_t)id.v * P.nplane + id.p) * P.nrad + id.r : 0;
+    const float mL = id.ok ? __ldg(&P.m[lor]) * L.L : 0.f;
 #pragma unroll
     for (int b = 0; b < TT; ++b) {
       q[b] = 0.f;
-      if (b < T) {
+      if (b < T && id.ok) {
         if (mode == MODE_SENS) {
           q[b] = mL;
         } else {
@@ -230,8 +242,8 @@ __global__ void __launch_bounds__(kBlock) k_grad(DevPlan P, int subset, const in
         any |= q[b] != 0.f;
       }
     }
-    if (mode != MODE_OBJ && any) back_lor<TT>(P, L, L.xdrive ? gT : g, q);
   }
+  if (mode != MODE_OBJ) back_lor<TT>(P, L, L.xdrive ? gT : g, q, any);
   if (kl_part) block_sum_store(kl, kl_part + blockIdx.x);
 }
 
@@ -240,16 +252,16 @@ __global__ void __launch_bounds__(kBlock) k_mult(DevPlan P, const float *__restr
                                                  const float *__restrict__ muT,
                                                  const float *__restrict__ sens, float *__restrict__ m) {
   const LorIdx id = lor_index(P, -1, (long long)blockIdx.x * blockDim.x + threadIdx.x);
-  if (!id.ok) return;
-  float s = sens ? __ldg(&sens[id.l]) : 1.f;
+  float s = (sens && id.ok) ? __ldg(&sens[id.l]) : 1.f;
   if (mu) {
-    Lor L;
-    lor_setup(P, id.v, id.p, id.r, L);
+    Lor L = {};
+    if (id.ok) lor_setup(P, id.v, id.p, id.r, L);
+    warp_uniform_range(L, id.ok);
     float acc[1];
-    forward_lor<1>(P, L, L.xdrive ? muT : mu, acc);
+    forward_lor<1>(P, L, L.xdrive ? muT : mu, acc, id.ok);
     s *= expf(-acc[0] * L.L);
   }
-  m[id.l] = s;
+  if (id.ok) m[id.l] = s;
 }
 
 // Tiled transpose of each z-slice: src [z][A][B] -> dst [z][B][A].  accumulate: 0 writes,
@@ -405,6 +417,7 @@ int grad_blocks(const DevPlan &P, int max_views) { return (int)blocks_for(P, max
 
 #define PET_TOF_DISPATCH(KERNEL, GRID, STREAM, ...)                             \
   do {                                                                         \
+    note_launch();                                                             \
     if (P.T <= 1) KERNEL<1><<<GRID, kBlock, 0, STREAM>>>(__VA_ARGS__);         \
     else if (P.T == 11) KERNEL<11><<<GRID, kBlock, 0, STREAM>>>(__VA_ARGS__);  \
     else if (P.T == 13) KERNEL<13><<<GRID, kBlock, 0, STREAM>>>(__VA_ARGS__);  \
@@ -457,6 +470,7 @@ cudaError_t launch_ratio(const DevPlan &P, int subset, const float *ax, float *q
                          int mode, cudaStream_t st) {
   const int grid = ratio_blocks(P, subset);
   if (grid == 0) return cudaSuccess;
+  note_launch();
   k_ratio<<<grid, kBlock, 0, st>>>(P, subset, ax, q, kl_part, mode);
   return cudaGetLastError();
 }
@@ -464,6 +478,7 @@ cudaError_t launch_ratio(const DevPlan &P, int subset, const float *ax, float *q
 cudaError_t launch_mult(const DevPlan &P, const float *mu, const float *muT, const float *sens,
                         float *m, cudaStream_t st) {
   const unsigned grid = blocks_for(P, P.nview);
+  note_launch();
   k_mult<<<grid, kBlock, 0, st>>>(P, mu, muT, sens, m);
   return cudaGetLastError();
 }
@@ -474,6 +489,7 @@ cudaError_t launch_transpose(const float *src, float *dst, int nx, int ny, int n
   // to_xfast = 1: xT[z][x][y] -> x[z][y][x]  (A = nx, B = ny)
   const int A = to_xfast ? nx : ny, B = to_xfast ? ny : nx;
   dim3 grid((B + 31) / 32, (A + 31) / 32, nz), block(32, 8);
+  note_launch();
   k_transpose<<<grid, block, 0, st>>>(const_cast<float *>(src), dst, A, B, accumulate);
   return cudaGetLastError();
 }

@@ -4,11 +4,13 @@
 // epoch is captured into a CUDA graph (one per epoch kind) and replayed after an
 // in-place parameter update.
 //
-// Every subset function shares the same prior term (beta/n) S (eq. 5), so the prior
-// part of the SAGA/SVRG estimator telescopes exactly:
-//   n((beta/n) grad S(x) - (beta/n) grad S(xhat)) + beta grad S(xhat) = beta grad S(x).
-// The gradient tables therefore hold data-term gradients only and the prior gradient
-// is evaluated once per iteration at the current iterate.
+// Every subset function shares the same prior term (beta/n) S (eq. 5).  In SVRG all
+// table entries belong to one snapshot xhat, so the prior part of eq. 9 telescopes
+// exactly:  n((beta/n) grad S(x) - (beta/n) grad S(xhat)) + beta grad S(xhat) = beta grad S(x);
+// the SVRG table therefore holds data-term gradients only.  SAGA's entries come from
+// different iterates and do not telescope, so its table holds full subset gradients
+// grad f_i = grad D_i + (beta/n) grad S, exactly as eq. 7 states.  The prior gradient
+// beta grad S(x) is evaluated once per iteration at the current iterate.
 #include <math.h>
 #include <string.h>
 
@@ -30,12 +32,14 @@ struct SolverState {  // device-resident scalars
 };
 
 struct UpdArgs {
-  float *x;
+  float *x, *xT;     // iterate, canonical [z][y][x] and transposed [z][x][y]
   const float *D;
-  float *g;          // subset data gradient (zeroed after use)
+  float *g, *gT;     // subset data gradient: canonical part and transposed part (x-driven
+                     // views); both are zeroed after use
   const float *gS;   // beta grad S(x)
   float *table;      // [n][N] data gradients (SAGA/SVRG)
   float *G;          // sum of table
+  int nx, ny, nz;
   size_t N;
   int n, subset;
   long long k;
@@ -64,40 +68,90 @@ __device__ __forceinline__ float step_of(const UpdArgs &a) {
   return (float)tau;
 }
 
-// ALGO: 0 SGD, 1 SAGA, 2 SVRG inner, 3 SVRG refresh (direction = full gradient).
+// Fused estimator + preconditioned step + prox (eq. 6 with eq. 7 / eq. 9) on a 32x32
+// tile of one slice.  The transposed gradient part is read through shared memory and
+// cleared; the new iterate is written in both layouts.  The stepsize is evaluated once
+// per block.  ALGO: 0 SGD, 1 SAGA, 2 SVRG inner, 3 SVRG refresh (direction = full
+// gradient at the snapshot).
 template <int ALGO>
-__global__ void k_update(UpdArgs a) {
-  const float tau = step_of(a);
-  if (blockIdx.x == 0 && threadIdx.x == 0 && a.tau_log) a.tau_log[a.k] = tau;
+__global__ void __launch_bounds__(256) k_update(UpdArgs a) {
+  __shared__ float tin[32][33];
+  __shared__ float tout[32][33];
+  __shared__ float s_tau;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32, z = blockIdx.z;
+  const size_t sl = (size_t)z * a.nx * a.ny;
+  if (tx == 0 && ty == 0) {
+    s_tau = step_of(a);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && z == 0 && a.tau_log) a.tau_log[a.k] = s_tau;
+  }
+  if (ALGO != 3) {
+    for (int j = ty; j < 32; j += 8) {
+      const int xx = x0 + j, yy = y0 + tx;
+      float v = 0.f;
+      if (xx < a.nx && yy < a.ny) {
+        const size_t o = sl + (size_t)xx * a.ny + yy;
+        v = a.gT[o];
+        a.gT[o] = 0.f;
+      }
+      tin[j][tx] = v;
+    }
+  }
+  __syncthreads();
+  const float tau = s_tau;
   const float nf = (float)a.n;
   float *Ti = a.table ? a.table + (size_t)a.subset * a.N : nullptr;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < a.N; i += (size_t)gridDim.x * blockDim.x) {
-    float dir;
-    if (ALGO == 0) {
-      dir = fmaf(nf, a.g[i], a.gS[i]);
-      a.g[i] = 0.f;
-    } else if (ALGO == 1) {
-      const float gi = a.g[i], ti = Ti[i], Gi = a.G[i];
-      dir = fmaf(nf, gi - ti, Gi) + a.gS[i];
-      a.G[i] = Gi + (gi - ti);
-      Ti[i] = gi;
-      a.g[i] = 0.f;
-    } else if (ALGO == 2) {
-      dir = fmaf(nf, a.g[i] - Ti[i], a.G[i]) + a.gS[i];
-      a.g[i] = 0.f;
-    } else {
-      dir = a.G[i] + a.gS[i];
+  for (int j = ty; j < 32; j += 8) {
+    const int xx = x0 + tx, yy = y0 + j;
+    float xn = 0.f;
+    if (xx < a.nx && yy < a.ny) {
+      const size_t i = sl + (size_t)yy * a.nx + xx;
+      float dir;
+      if (ALGO == 3) {
+        dir = a.G[i] + a.gS[i];
+      } else {
+        const float gi = a.g[i] + tin[tx][j];
+        a.g[i] = 0.f;
+        if (ALGO == 0) {
+          dir = fmaf(nf, gi, a.gS[i]);
+        } else if (ALGO == 1) {
+          const float gf = fmaf(a.gS[i], 1.f / nf, gi);  // grad f_i = grad D_i + (beta/n) grad S
+          const float ti = Ti[i], Gi = a.G[i];
+          dir = fmaf(nf, gf - ti, Gi);
+          a.G[i] = Gi + (gf - ti);
+          Ti[i] = gf;
+        } else {
+          dir = fmaf(nf, gi - Ti[i], a.G[i]) + a.gS[i];
+        }
+      }
+      xn = fmaf(-tau * a.D[i], dir, a.x[i]);
+      xn = xn > 0.f ? xn : 0.f;
+      a.x[i] = xn;
     }
-    const float xn = fmaf(-tau * a.D[i], dir, a.x[i]);
-    a.x[i] = xn > 0.f ? xn : 0.f;
+    tout[tx][j] = xn;
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int xx = x0 + j, yy = y0 + tx;
+    if (xx < a.nx && yy < a.ny) a.xT[sl + (size_t)xx * a.ny + yy] = tout[j][tx];
   }
 }
 
-// G = sum_s table[s]
-__global__ void k_sum_table(const float *__restrict__ table, float *__restrict__ G, int n, size_t N) {
+// G = sum_s table[s]; with gS != NULL every entry first receives the prior share
+// gS/n (SAGA's full subset gradients).
+__global__ void k_sum_table(float *__restrict__ table, float *__restrict__ G, const float *__restrict__ gS,
+                            int n, size_t N) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    const float pr = gS ? gS[i] * (1.f / (float)n) : 0.f;
     float s = 0.f;
-    for (int t = 0; t < n; ++t) s += table[(size_t)t * N + i];
+    for (int t = 0; t < n; ++t) {
+      float v = table[(size_t)t * N + i];
+      if (gS) {
+        v += pr;
+        table[(size_t)t * N + i] = v;
+      }
+      s += v;
+    }
     G[i] = s;
   }
 }
@@ -140,9 +194,11 @@ __global__ void k_bb_dots(const float *__restrict__ x, float *__restrict__ xhat_
 }
 
 __global__ void k_bb_final(const double *part, int nb, SolverState *st) {
-  if (threadIdx.x != 0) return;
   double pq = 0.0, qq = 0.0;
-  for (int b = 0; b < nb; ++b) { pq += part[2 * b]; qq += part[2 * b + 1]; }
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) { pq += part[2 * b]; qq += part[2 * b + 1]; }
+  pq = warp_block_sum(pq);
+  qq = warp_block_sum(qq);
+  if (threadIdx.x != 0) return;
   st->dots[0] = pq;
   st->dots[1] = qq;
   if (st->have_snapshot && qq > 0.0) {
@@ -183,6 +239,15 @@ struct pet_solver {
   bool initialised = false;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t exec[2] = {nullptr, nullptr};  // [0] plain epoch, [1] epoch starting with a refresh
+  // optional event timing of the fused subset-gradient kernel: one (start, stop) pair per
+  // launch slot of an SVRG outer loop (or of an epoch for SGD/SAGA)
+  bool profile = false;
+  std::vector<cudaEvent_t> ev0, ev1;
+  std::vector<char> pending;
+  std::vector<int> kind_slots[2];
+  double prof_ms = 0.0;
+  long long prof_n = 0;
+  int capturing_kind = 0;
 };
 
 static pet_status grow_tau_log(pet_solver *s, long long need) {
@@ -207,6 +272,8 @@ static void solver_free(pet_solver *s) {
   for (auto &e : s->exec)
     if (e) cudaGraphExecDestroy(e);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  for (auto e : s->ev0) cudaEventDestroy(e);
+  for (auto e : s->ev1) cudaEventDestroy(e);
   cudaFree(s->x); cudaFree(s->D); cudaFree(s->g); cudaFree(s->gS); cudaFree(s->H);
   cudaFree(s->table); cudaFree(s->G); cudaFree(s->xhat_old); cudaFree(s->Gfull_old);
   cudaFree(s->part); cudaFree(s->st); cudaFree(s->tau_log);
@@ -302,15 +369,46 @@ static int subset_of(pet_solver *s, long long k) {
     if ((call) != cudaSuccess) return PET_ERR_CUDA; \
   } while (0)
 
+static int n_slots(const pet_solver *s) {
+  return s->o.algo == PET_SVRG ? s->n + s->o.omega * s->n : s->n;
+}
+
+// Launch slot of the subset-gradient kernel: unique within one SVRG outer loop
+// (refresh gradients 0..n-1, inner iterations after them) or one SGD/SAGA epoch.
+static int slot_of(const pet_solver *s, long long k, int refresh_sub) {
+  if (s->o.algo == PET_SVRG) {
+    const long long kk = k % ((long long)s->o.omega * s->n);
+    return refresh_sub >= 0 ? refresh_sub : (int)(s->n + kk - 1);
+  }
+  return (int)(k % s->n);
+}
+
+static cudaError_t record(pet_solver *s, cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  return cudaEventRecordWithFlags(ev, st, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                               : cudaEventRecordDefault);
+}
+
 // Data gradient of subset `sub` at x into `dst` (zeroed by the caller unless deterministic).
-static pet_status data_grad(pet_solver *s, int sub, float *dst, cudaStream_t st) {
+static pet_status data_grad(pet_solver *s, int sub, float *dst, cudaStream_t st, int slot = -1,
+                            bool combine = true) {
   pet_plan *p = s->plan;
   if (s->o.deterministic) {
     pet_status e = pet_objective_grad(p, sub, s->x, dst, nullptr, nullptr, PET_GRAD_DETERMINISTIC, st);
     return e;
   }
+  const bool prof = s->profile && slot >= 0 && slot < (int)s->ev0.size();
+  if (prof) SCK(record(s, s->ev0[slot], st));
   SCK(launch_grad(p->dp, sub, nullptr, s->x, p->d_xT, dst, p->d_gT, nullptr, MODE_GRAD, nullptr, st));
-  SCK(launch_transpose(p->d_gT, dst, p->g.nx, p->g.ny, p->g.nz, 1, 2, st));  // add and clear
+  if (prof) {
+    SCK(record(s, s->ev1[slot], st));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs == cudaStreamCaptureStatusActive) s->kind_slots[s->capturing_kind].push_back(slot);
+    else s->pending[slot] = 1;
+  }
+  if (combine) SCK(launch_transpose(p->d_gT, dst, p->g.nx, p->g.ny, p->g.nz, 1, 2, st));  // add and clear
   return PET_OK;
 }
 
@@ -334,11 +432,19 @@ static pet_status precond_update(pet_solver *s, cudaStream_t st) {
 
 static UpdArgs upd_args(pet_solver *s, int sub, long long k) {
   UpdArgs a;
-  a.x = s->x; a.D = s->D; a.g = s->g; a.gS = s->gS; a.table = s->table; a.G = s->G;
+  pet_plan *p = s->plan;
+  a.x = s->x; a.xT = p->d_xT; a.D = s->D; a.g = s->g; a.gT = p->d_gT; a.gS = s->gS;
+  a.table = s->table; a.G = s->G;
+  a.nx = p->g.nx; a.ny = p->g.ny; a.nz = p->g.nz;
   a.N = s->N; a.n = s->n; a.subset = sub < 0 ? 0 : sub; a.k = k;
   a.rule = s->o.step_rule; a.tau0 = (float)s->o.tau0; a.eta = (float)s->o.eta;
   a.st = s->st; a.tau_log = s->tau_log;
   return a;
+}
+
+static dim3 tile_grid(const pet_solver *s) {
+  const pet_geometry &g = s->plan->g;
+  return dim3((g.nx + 31) / 32, (g.ny + 31) / 32, g.nz);
 }
 
 // SAGA table initialisation: all entries at the start image (no step).
@@ -351,7 +457,9 @@ static pet_status saga_init(pet_solver *s, cudaStream_t st) {
     pet_status e = data_grad(s, t, Tt, st);
     if (e != PET_OK) return e;
   }
-  k_sum_table<<<grid_elems(s->N), 256, 0, st>>>(s->table, s->G, s->n, s->N);
+  SCK(launch_rdp(prior_args(s, s->o.beta), s->x, s->gS, nullptr, nullptr, 0, nullptr, st));
+  note_launch();
+  k_sum_table<<<grid_elems(s->N), 256, 0, st>>>(s->table, s->G, s->gS, s->n, s->N);
   SCK(cudaGetLastError());
   return PET_OK;
 }
@@ -366,28 +474,34 @@ static pet_status iterate(pet_solver *s, long long k, int sub, cudaStream_t st) 
     }
   const unsigned ge = grid_elems(s->N);
   const bool refresh = s->o.algo == PET_SVRG && k % ((long long)s->o.omega * s->n) == 0;
-  SCK(to_frames(p, s->x, st));
+  // the transposed copy of x is kept current by the update kernel
+  (void)p;
   if (refresh) {
     for (int t = 0; t < s->n; ++t) {
       float *Tt = s->table + (size_t)t * s->N;
       if (!s->o.deterministic) SCK(cudaMemsetAsync(Tt, 0, s->N * 4, st));
-      pet_status e = data_grad(s, t, Tt, st);
+      pet_status e = data_grad(s, t, Tt, st, slot_of(s, k, t));
       if (e != PET_OK) return e;
     }
-    k_sum_table<<<ge, 256, 0, st>>>(s->table, s->G, s->n, s->N);
+    note_launch();
+    k_sum_table<<<ge, 256, 0, st>>>(s->table, s->G, nullptr, s->n, s->N);
     SCK(launch_rdp(prior_args(s, s->o.beta), s->x, s->gS, nullptr, nullptr, 0, nullptr, st));
+    note_launch();
     k_bb_dots<<<ge, 256, 0, st>>>(s->x, s->xhat_old, s->G, s->gS, s->Gfull_old, s->N, s->part);
-    k_bb_final<<<1, 32, 0, st>>>(s->part, (int)ge, s->st);
-    k_update<3><<<ge, 256, 0, st>>>(upd_args(s, -1, k));
+    note_launch();
+    k_bb_final<<<1, 256, 0, st>>>(s->part, (int)ge, s->st);
+    note_launch();
+    k_update<3><<<tile_grid(s), dim3(32, 8), 0, st>>>(upd_args(s, -1, k));
   } else {
     if (sub < 0) return PET_ERR_ARG;
-    pet_status e = data_grad(s, sub, s->g, st);
+    pet_status e = data_grad(s, sub, s->g, st, slot_of(s, k, -1), false);
     if (e != PET_OK) return e;
     SCK(launch_rdp(prior_args(s, s->o.beta), s->x, s->gS, nullptr, nullptr, 0, nullptr, st));
     const UpdArgs a = upd_args(s, sub, k);
-    if (s->o.algo == PET_SGD) k_update<0><<<ge, 256, 0, st>>>(a);
-    else if (s->o.algo == PET_SAGA) k_update<1><<<ge, 256, 0, st>>>(a);
-    else k_update<2><<<ge, 256, 0, st>>>(a);
+    note_launch();
+    if (s->o.algo == PET_SGD) k_update<0><<<tile_grid(s), dim3(32, 8), 0, st>>>(a);
+    else if (s->o.algo == PET_SAGA) k_update<1><<<tile_grid(s), dim3(32, 8), 0, st>>>(a);
+    else k_update<2><<<tile_grid(s), dim3(32, 8), 0, st>>>(a);
   }
   SCK(cudaGetLastError());
   return PET_OK;
@@ -405,6 +519,8 @@ extern "C" pet_status pet_solver_run(pet_solver *s, long long niter, void *strea
   if (!s->order.empty() && s->k + niter > (long long)s->order.size()) return PET_ERR_ARG;
   pet_status e = grow_tau_log(s, s->k + niter);
   if (e != PET_OK) return e;
+  // the plan's transposed image may have been used by other calls since the last run
+  SCK(to_frames(s->plan, s->x, st));
   if (!s->initialised) {
     if (s->o.algo == PET_SAGA) {
       e = saga_init(s, st);
@@ -422,10 +538,15 @@ extern "C" pet_status pet_solver_run(pet_solver *s, long long niter, void *strea
       std::vector<int> subs(n);
       for (int j = 0; j < n; ++j) subs[j] = subset_of(s, k0 + j);
       cudaGraph_t graph = nullptr;
+      s->capturing_kind = kind;
+      s->kind_slots[kind].clear();
+      const long long before = launch_count();
       SCK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
       pet_status ie = PET_OK;
       for (int j = 0; j < n && ie == PET_OK; ++j) ie = iterate(s, k0 + j, subs[j], s->cap_stream);
       cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &graph);
+      const long long captured = launch_count() - before;  // nodes, not launches yet
+      note_launch(-captured);
       if (ie != PET_OK) { if (graph) cudaGraphDestroy(graph); return ie; }
       if (ce != cudaSuccess) return PET_ERR_CUDA;
       bool updated = false;
@@ -442,6 +563,8 @@ extern "C" pet_status pet_solver_run(pet_solver *s, long long niter, void *strea
       }
       cudaGraphDestroy(graph);
       SCK(cudaGraphLaunch(s->exec[kind], st));
+      note_launch(captured);
+      for (int sl : s->kind_slots[kind]) s->pending[sl] = 1;
       s->k = k0 + n;
     } else {
       const int sub = subset_of(s, k0);
@@ -452,3 +575,41 @@ extern "C" pet_status pet_solver_run(pet_solver *s, long long niter, void *strea
   }
   return PET_OK;
 }
+
+extern "C" pet_status pet_solver_profile(pet_solver *s, int enable) {
+  if (!s) return PET_ERR_ARG;
+  if (enable && s->ev0.empty()) {
+    const int ns = n_slots(s);
+    s->ev0.resize(ns);
+    s->ev1.resize(ns);
+    s->pending.assign(ns, 0);
+    for (int i = 0; i < ns; ++i)
+      if (cudaEventCreate(&s->ev0[i]) != cudaSuccess || cudaEventCreate(&s->ev1[i]) != cudaSuccess)
+        return PET_ERR_CUDA;
+  }
+  s->profile = enable != 0;
+  for (auto &e : s->exec)
+    if (e) { cudaGraphExecDestroy(e); e = nullptr; }
+  return PET_OK;
+}
+
+extern "C" pet_status pet_solver_kernel_time(pet_solver *s, double *total_ms, long long *launches) {
+  if (!s || !total_ms || !launches) return PET_ERR_ARG;
+  for (size_t i = 0; i < s->pending.size(); ++i) {
+    if (!s->pending[i]) continue;
+    float ms = 0.f;
+    if (cudaEventSynchronize(s->ev1[i]) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, s->ev0[i], s->ev1[i]) != cudaSuccess)
+      return PET_ERR_CUDA;
+    s->prof_ms += ms;
+    s->prof_n += 1;
+    s->pending[i] = 0;
+  }
+  *total_ms = s->prof_ms;
+  *launches = s->prof_n;
+  s->prof_ms = 0.0;
+  s->prof_n = 0;
+  return PET_OK;
+}
+
+extern "C" long long pet_launch_count(void) { return launch_count(); }
