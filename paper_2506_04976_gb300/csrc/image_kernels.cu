@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(RDP_TX * RDP_TY) k_rdp(RdpArgs a, const float 
             const float d = xi - xj;
             const float ad = fabsf(d);
             const float phi = (xi + xj) + a.gamma * ad + a.eps;
-            const float inv = __frcp_rn(phi);
+            const float inv = __fdividef(1.f, phi);
             const float inv2 = inv * inv;
             gsum = fmaf(w * d * ((2.f * phi - d) - a.gamma * ad), inv2, gsum);
             const float e2 = fmaf(2.f, xj, a.eps);

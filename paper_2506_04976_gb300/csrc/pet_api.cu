@@ -136,7 +136,8 @@ extern "C" pet_status pet_plan_create(const pet_geometry *geom, pet_plan **out) 
     dp.tof_erfc_amax = (float)erfc(amax);
     dp.tof_half_norm = (float)(1.0 / (2.0 * erf(amax)));
   }
-  const int gb_all = grad_blocks(dp, V);
+  // any fused-gradient launch (up to 4 parts per LOR) has at most this many blocks
+  const int gb_all = (int)((4 * nlor + kBlock - 1) / kBlock) + 1;
   const int rb = ratio_blocks(dp, -1);
   pl->npart = std::max({gb_all, rb, rdp_blocks(g.nx, g.ny, g.nz), 4 * nrmse_blocks(pl->N), 1});
   bool ok = dalloc(&pl->d_view, V) == cudaSuccess && dalloc(&pl->d_vr, (size_t)V * R) == cudaSuccess &&

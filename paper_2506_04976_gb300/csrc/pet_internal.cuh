@@ -102,8 +102,9 @@ __device__ __forceinline__ void warp_uniform_range(Lor &L, bool valid) {
   const bool own = valid && L.i0 <= L.i1;
   const int lo = __reduce_min_sync(0xffffffffu, own ? L.i0 : 0x7fffffff);
   const int hi = __reduce_max_sync(0xffffffffu, own ? L.i1 : -1);
-  L.i0 = lo;
-  L.i1 = hi;
+  // an empty union becomes [0, -1]: loops start at i0 + part and must not overflow
+  L.i0 = lo <= hi ? lo : 0;
+  L.i1 = lo <= hi ? hi : -1;
 }
 
 // Bilinear sample position at plane i.
@@ -120,10 +121,12 @@ __device__ __forceinline__ void sample_at(const Lor &L, int i, int Na, int Nb, i
   const int ib = (int)fbf, iz = (int)fzf;
   S.wb = fb - fbf;
   S.wz = fz - fzf;
+  // neighbours outside the image, or with an exactly-zero weight (e.g. the upper row of
+  // a direct plane, whose axial coordinate is an exact slice index), are skipped
   S.b0 = (unsigned)ib < (unsigned)Nb;
-  S.b1 = (unsigned)(ib + 1) < (unsigned)Nb;
+  S.b1 = (unsigned)(ib + 1) < (unsigned)Nb && S.wb != 0.f;
   S.z0 = (unsigned)iz < (unsigned)Nz;
-  S.z1 = (unsigned)(iz + 1) < (unsigned)Nz;
+  S.z1 = (unsigned)(iz + 1) < (unsigned)Nz && S.wz != 0.f;
   S.base = (iz * Na + i) * Nb + ib;
 }
 

@@ -46,10 +46,10 @@ __device__ __forceinline__ int tof_bins(const DevPlan &P) {
 
 // Forward: acc[b] = sum over samples of bilinear(x) * w_b(t) (compensated); the step
 // length L is applied by the caller.
-template <int TT>
+template <int TT, int STRIDE = 1>
 __device__ __forceinline__ void forward_lor(const DevPlan &P, const Lor &L,
                                             const float *__restrict__ img, float (&acc)[TT],
-                                            bool act = true) {
+                                            bool act = true, int off = 0) {
   const int Na = L.xdrive ? P.nx : P.ny;
   const int Nb = L.xdrive ? P.ny : P.nx;
   const int plane = Na * Nb;
@@ -58,7 +58,7 @@ __device__ __forceinline__ void forward_lor(const DevPlan &P, const Lor &L,
 #pragma unroll
   for (int b = 0; b < TT; ++b) { acc[b] = 0.f; cmp[b] = 0.f; }
   const float du = P.tof_w * P.tof_inv;
-  for (int i = L.i0; i <= L.i1; ++i) {
+  for (int i = L.i0 + off; i <= L.i1; i += STRIDE) {
     if (!act || i >= Na) continue;
     Samp S;
     sample_at(L, i, Na, Nb, P.nz, S);
@@ -85,15 +85,15 @@ __device__ __forceinline__ void forward_lor(const DevPlan &P, const Lor &L,
 }
 
 // Back: scatter sum_b q[b] w_b(t) * bilinear weights; q already includes m and L.
-template <int TT>
+template <int TT, int STRIDE = 1>
 __device__ __forceinline__ void back_lor(const DevPlan &P, const Lor &L, float *__restrict__ img,
-                                         const float (&q)[TT], bool act = true) {
+                                         const float (&q)[TT], bool act = true, int off = 0) {
   const int Na = L.xdrive ? P.nx : P.ny;
   const int Nb = L.xdrive ? P.ny : P.nx;
   const int plane = Na * Nb;
   const int T = tof_bins<TT>(P);
   const float du = P.tof_w * P.tof_inv;
-  for (int i = L.i0; i <= L.i1; ++i) {
+  for (int i = L.i0 + off; i <= L.i1; i += STRIDE) {
     if (!act || i >= Na) continue;
     Samp S;
     sample_at(L, i, Na, Nb, P.nz, S);
@@ -197,19 +197,43 @@ __device__ __forceinline__ void block_sum_store(double v, double *out) {
 }
 
 // Fused subset gradient: forward, KL ratio, backprojection; optional FP64 KL partials.
-template <int TT>
+// The block covers kBlock/SPLIT LORs; part j of the block (warps j*W .. (j+1)*W-1)
+// takes the planes i = i0 + j, i0 + j + SPLIT, ... of the warp-uniform plane range, so
+// the parts carry equal work.  The forward partial sums are exchanged through shared
+// memory at a block barrier and added in a fixed order, so every part sees the same
+// ybar; each part then backprojects its own planes.  SPLIT multiplies the parallelism of launches with few
+// LORs (one subset of a small scanner).
+template <int TT, int SPLIT>
 __global__ void __launch_bounds__(kBlock) k_grad(DevPlan P, int subset, const int *subset_dev,
                                                  const float *__restrict__ x, const float *__restrict__ xT,
                                                  float *__restrict__ g, float *__restrict__ gT,
                                                  double *__restrict__ kl_part, int mode) {
+  constexpr int LPB = kBlock / SPLIT;  // LORs per block
+  __shared__ float xs[SPLIT > 1 ? SPLIT : 1][SPLIT > 1 ? LPB : 1][TT];
   if (subset_dev) subset = *subset_dev;
-  const LorIdx id = lor_index(P, subset, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+  const int part = threadIdx.x / LPB;
+  const int tl = threadIdx.x % LPB;
+  const LorIdx id = lor_index(P, subset, (long long)blockIdx.x * LPB + tl);
   double kl = 0.0;
   Lor L = {};
   if (id.ok) lor_setup(P, id.v, id.p, id.r, L);
   warp_uniform_range(L, id.ok);
   float acc[TT];
-  if (mode != MODE_SENS) forward_lor<TT>(P, L, L.xdrive ? xT : x, acc, id.ok);
+  if (mode != MODE_SENS) {
+    forward_lor<TT, SPLIT>(P, L, L.xdrive ? xT : x, acc, id.ok, part);
+    if (SPLIT > 1) {
+#pragma unroll
+      for (int b = 0; b < TT; ++b) xs[part][tl][b] = acc[b];
+      __syncthreads();
+#pragma unroll
+      for (int b = 0; b < TT; ++b) {
+        float t = xs[0][tl][b];
+#pragma unroll
+        for (int j = 1; j < SPLIT; ++j) t += xs[j][tl][b];
+        acc[b] = t;
+      }
+    }
+  }
   float q[TT];
   bool any = false;
   {
@@ -226,14 +250,15 @@ __global__ void __launch_bounds__(kBlock) k_grad(DevPlan P, int subset, const in
           const size_t bi = lor * T + b;
           const float ybar = fmaf(mL, acc[b], __ldg(&P.r[bi]));
           const float yb = load_y(P, bi);
+          const bool count = kl_part && part == 0;
           if (!(ybar > 0.f)) {
             if (yb > 0.f) atomicOr(P.err, 1);
             q[b] = (mode == MODE_GRAD && yb == 0.f) ? mL : 0.f;
-            if (kl_part && yb == 0.f) kl += (double)fmaxf(ybar, 0.f);
+            if (count && yb == 0.f) kl += (double)fmaxf(ybar, 0.f);
           } else {
             if (mode == MODE_GRAD) q[b] = mL * (1.f - yb / ybar);
             else if (mode == MODE_EM) q[b] = mL * (yb / ybar);
-            if (kl_part) {
+            if (count) {
               const double db = ybar, dy = yb;
               kl += (yb > 0.f) ? (db - dy + dy * log(dy / db)) : db;
             }
@@ -243,7 +268,7 @@ __global__ void __launch_bounds__(kBlock) k_grad(DevPlan P, int subset, const in
       }
     }
   }
-  if (mode != MODE_OBJ) back_lor<TT>(P, L, L.xdrive ? gT : g, q, any);
+  if (mode != MODE_OBJ) back_lor<TT, SPLIT>(P, L, L.xdrive ? gT : g, q, any, part);
   if (kl_part) block_sum_store(kl, kl_part + blockIdx.x);
 }
 
@@ -413,7 +438,6 @@ static unsigned blocks_for(const DevPlan &P, int nviews) {
   return (unsigned)((n + kBlock - 1) / kBlock);
 }
 
-int grad_blocks(const DevPlan &P, int max_views) { return (int)blocks_for(P, max_views); }
 
 #define PET_TOF_DISPATCH(KERNEL, GRID, STREAM, ...)                             \
   do {                                                                         \
@@ -441,15 +465,43 @@ cudaError_t launch_back(const DevPlan &P, int subset, const float *q, float *g, 
   return cudaGetLastError();
 }
 
+// Parts per LOR: enough threads for about two full waves (152 SMs x 2048 threads).
+static int split_for(long long nlor) {
+  const long long target = 2LL * 152 * 2048;
+  if (nlor * 2 > target) return 1;
+  if (nlor * 4 > target) return 2;
+  return 4;
+}
+
+int grad_blocks(const DevPlan &P, int max_views) {
+  const long long nlor = (long long)max_views * P.nplane * P.nrad;
+  const int lpb = kBlock / split_for(nlor);
+  return (int)((nlor + lpb - 1) / lpb);
+}
+
+#define PET_GRAD_LAUNCH(SPLIT)                                                                  \
+  do {                                                                                         \
+    if (P.T <= 1) k_grad<1, SPLIT><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);   \
+    else if (P.T == 11) k_grad<11, SPLIT><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode); \
+    else if (P.T == 13) k_grad<13, SPLIT><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode); \
+    else if (P.T <= 16) k_grad<16, SPLIT><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode); \
+    else k_grad<32, SPLIT><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);           \
+  } while (0)
+
 cudaError_t launch_grad(const DevPlan &P, int subset, const int *subset_dev, const float *x,
                         const float *xT, float *g, float *gT, double *kl_part, int mode,
                         int *nblocks_out, cudaStream_t st) {
   // with a device-side subset index the grid covers the largest subset
   const int nv = subset_dev ? (P.nview + P.nsub - 1) / P.nsub : views_in(P, subset);
-  const unsigned grid = blocks_for(P, nv);
+  const long long nlor = (long long)nv * P.nplane * P.nrad;
+  const int split = split_for(nlor);
+  const unsigned grid = (unsigned)grad_blocks(P, nv);
   if (nblocks_out) *nblocks_out = (int)grid;
   if (grid == 0) return cudaSuccess;
-  PET_TOF_DISPATCH(k_grad, grid, st, P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
+  note_launch();
+  if (split == 4) PET_GRAD_LAUNCH(4);
+  else if (split == 2) PET_GRAD_LAUNCH(2);
+  else PET_GRAD_LAUNCH(1);
   return cudaGetLastError();
 }
 
