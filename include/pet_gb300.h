@@ -143,6 +143,25 @@ pet_status pet_em_update(pet_plan *plan, int subset, float *x, void *stream);
 pet_status pet_rdp(const pet_rdp_params *p, const float *x, float *grad, float *hdiag,
                    double *val, int accumulate, void *stream);
 
+/* Allocation-free variant of pet_rdp (the paper has no counterpart; this exists for
+ * callers that cannot allocate device memory while running, e.g. a service whose
+ * device memory is fully reserved at start-up, or a host framework that forbids
+ * allocations outside its own allocator).  Same arguments, outputs and errors as
+ * pet_rdp, but the FP64 partial sums of the value live in a fixed array inside this
+ * library (PET_RDP_STATIC_MAX_PARTIALS doubles, 512 KiB, held by every GPU that loads
+ * the library until the process exits) and the call allocates nothing.
+ *   - Images needing more than PET_RDP_STATIC_MAX_PARTIALS stencil blocks of 32x8x8
+ *     voxels (more than about 134 million voxels) are rejected with
+ *     PET_ERR_UNSUPPORTED when val is requested.
+ *   - The first call on a device (with val != NULL) looks up the array's device
+ *     address with that device current; make that first call before any stream
+ *     capture.  Later calls only reuse the cached address.
+ *   - All calls share the one array, which keeps the last call's contents.  Calls
+ *     that overlap on the GPU (different streams without ordering) race on it. */
+#define PET_RDP_STATIC_MAX_PARTIALS 65536
+pet_status pet_rdp_static(const pet_rdp_params *p, const float *x, float *grad, float *hdiag,
+                          double *val, int accumulate, void *stream);
+
 /* Diagonal preconditioner of Sec. 2.3 with delta = delta_rel * max(x):
  * hdiag_betaS == NULL: D_MLEM = (x+delta)/A^T 1;
  * otherwise the harmonic form of eq. 8: (x+delta)/(A^T 1 + alpha hdiag_betaS (x+delta)).
