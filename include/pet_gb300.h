@@ -150,8 +150,8 @@ pet_status pet_rdp(const pet_rdp_params *p, const float *x, float *grad, float *
  * pet_rdp, but the FP64 partial sums of the value live in a fixed array inside this
  * library (PET_RDP_STATIC_MAX_PARTIALS doubles, 512 KiB, held by every GPU that loads
  * the library until the process exits) and the call allocates nothing.
- *   - Images needing more than PET_RDP_STATIC_MAX_PARTIALS stencil blocks of 32x8x8
- *     voxels (more than about 134 million voxels) are rejected with
+ *   - Images needing more than PET_RDP_STATIC_MAX_PARTIALS stencil blocks of 32x8x4
+ *     voxels (more than about 67 million voxels) are rejected with
  *     PET_ERR_UNSUPPORTED when val is requested.
  *   - The first call on a device (with val != NULL) looks up the array's device
  *     address with that device current; make that first call before any stream

@@ -8,7 +8,7 @@
 
 namespace petgb {
 
-constexpr int RDP_TX = 32, RDP_TY = 8, RDP_ZCH = 8;
+constexpr int RDP_TX = 32, RDP_TY = 8, RDP_ZCH = 4;
 
 RdpArgs make_rdp_args(const pet_rdp_params &p) {
   RdpArgs a;

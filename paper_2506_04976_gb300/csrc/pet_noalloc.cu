@@ -14,8 +14,8 @@ using namespace petgb;
 namespace {
 
 // Scratch for the per-block FP64 partial sums of S(x): PET_RDP_STATIC_MAX_PARTIALS
-// doubles (512 KiB), enough for images of up to 65536 stencil blocks of 32x8x8 voxels
-// (134 million voxels).  Every GPU that loads the library holds this array until the
+// doubles (512 KiB), enough for images of up to 65536 stencil blocks of 32x8x4 voxels
+// (67 million voxels).  Every GPU that loads the library holds this array until the
 // process exits.
 __device__ __align__(256) double g_rdp_partials[PET_RDP_STATIC_MAX_PARTIALS];
 
