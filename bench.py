@@ -206,6 +206,7 @@ def run_grad_only(args, pet, dev):
     plan.set_data(torch.from_numpy(p["y"].view(np.int16)).to(dev), torch.from_numpy(p["r"]).to(dev),
                   torch.from_numpy(p["mu"].astype(np.float32)).to(dev),
                   torch.from_numpy(p["sens"].astype(np.float32)).to(dev))
+    plan.autotune()
     x = torch.from_numpy(np.maximum(p["x_true"], 0.05 * p["x_true"].max()).astype(np.float32)).to(dev)
     gbuf = torch.empty_like(x)
     for i in range(args.warmup):
@@ -251,6 +252,7 @@ def main():
     r = r_host.to(dev)
     plan.set_data(y, r, torch.from_numpy(p["mu"].astype(np.float32)).to(dev),
                   torch.from_numpy(p["sens"].astype(np.float32)).to(dev))
+    shape = plan.autotune()
     # one OSEM epoch from a uniform image (Sec. 3.1 initialisation)
     x0 = torch.ones(plan.img_shape, device=dev)
     for s in range(n):
@@ -344,7 +346,8 @@ def main():
                 "frac": achieved / peak, "traffic": ncu_traffic("k_grad_c2"),
                 "kernel": "k_grad<1> (fused forward, KL ratio, backprojection of one subset)",
                 "kernel_ms": kavg, "launches_timed": kern_n, "algorithmic_bytes": abytes,
-                "peak_kind": f"hbm_gbs {peak_kind}"}
+                "peak_kind": f"hbm_gbs {peak_kind}", "launch_shape": {"planes_per_thread": shape[0],
+                                                                      "parts_per_lor": shape[1]}}
     cpu = None
     if world == 1 and not args.no_cpu:
         times = cpu_baseline(p, args.cpu_seconds)

@@ -85,6 +85,8 @@ _sigs = {
     "pet_plan_mult": (_vp, [_vp]),
     "pet_plan_sensitivity": (_vp, [_vp, C.c_int]),
     "pet_plan_check": (C.c_int, [_vp, _vp]),
+    "pet_plan_set_grad_shape": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "pet_plan_autotune": (C.c_int, [_vp, _vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "pet_forward": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
     "pet_back": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, _vp]),
     "pet_objective_grad": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, C.POINTER(RdpParams), C.c_int, _vp]),
@@ -200,6 +202,16 @@ class Plan:
 
     def sensitivity(self, s=-1):
         return _wrap(_lib.pet_plan_sensitivity(self._h, int(s)), self.img_shape)
+
+    def set_grad_shape(self, planes_per_thread=0, parts=0):
+        _ck(_lib.pet_plan_set_grad_shape(self._h, int(planes_per_thread), int(parts)),
+            "pet_plan_set_grad_shape")
+
+    def autotune(self):
+        """Times the fused-gradient launch shapes and keeps the fastest; returns it."""
+        k, sp = C.c_int(), C.c_int()
+        _ck(_lib.pet_plan_autotune(self._h, _stream(), C.byref(k), C.byref(sp)), "pet_plan_autotune")
+        return k.value, sp.value
 
     def check(self):
         _ck(_lib.pet_plan_check(self._h, _stream()), "pet_plan_check")

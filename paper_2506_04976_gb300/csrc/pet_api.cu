@@ -347,3 +347,73 @@ extern "C" pet_status pet_nrmse(const float *x, const float *ref, const uint8_t 
   cudaFreeAsync(part, st);
   return e == cudaSuccess ? PET_OK : PET_ERR_CUDA;
 }
+
+extern "C" pet_status pet_plan_set_grad_shape(pet_plan *plan, int planes_per_thread, int parts) {
+  if (!plan) return PET_ERR_ARG;
+  const bool kok = planes_per_thread == 0 || planes_per_thread == 1 ||
+                   ((planes_per_thread == 2 || planes_per_thread == 4) && plan->T == 1);
+  const bool sok = parts == 0 || parts == 1 || parts == 2 || parts == 4;
+  if (!kok || !sok) return PET_ERR_ARG;
+  plan->dp.grad_k = planes_per_thread;
+  plan->dp.grad_split = parts;
+  return PET_OK;
+}
+
+extern "C" pet_status pet_plan_autotune(pet_plan *plan, void *stream, int *planes_per_thread, int *parts) {
+  if (!plan) return PET_ERR_ARG;
+  if (!plan->has_data) return PET_ERR_STATE;
+  cudaStream_t st = S(stream);
+  const int ks[3] = {1, 2, 4}, ss[3] = {1, 2, 4};
+  float *x = plan->d_img, *g = nullptr;
+  if (dalloc(&g, plan->N) != cudaSuccess) return PET_ERR_NOMEM;  // setup-time temporary
+  if (launch_fill(x, plan->N, 1.f, st) != cudaSuccess) { cudaFree(g); return PET_ERR_CUDA; }
+  cudaEvent_t e0, e1;
+  if (to_frames(plan, x, st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess) {
+    cudaFree(g);
+    return PET_ERR_CUDA;
+  }
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    cudaFree(g);
+    return PET_ERR_CUDA;
+  }
+  const int old_k = plan->dp.grad_k, old_s = plan->dp.grad_split;
+  float best = 1e30f;
+  int bk = 1, bs = 1;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      if (ks[a] > 1 && plan->T > 1) continue;
+      plan->dp.grad_k = ks[a];
+      plan->dp.grad_split = ss[b];
+      float ms = 0.f;
+      bool fail = false;
+      for (int it = 0; it < 6 && !fail; ++it) {
+        if (it == 2) fail |= cudaEventRecord(e0, st) != cudaSuccess;
+        fail |= launch_grad(plan->dp, 0, nullptr, x, plan->d_xT, g, plan->d_gT, nullptr, MODE_GRAD, nullptr, st) !=
+                cudaSuccess;
+      }
+      fail |= cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess;
+      if (fail) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaStreamSynchronize(st);
+        cudaFree(g);
+        plan->dp.grad_k = old_k;
+        plan->dp.grad_split = old_s;
+        return PET_ERR_CUDA;
+      }
+      if (ms < best) { best = ms; bk = ks[a]; bs = ss[b]; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
+  cudaFree(g);
+  plan->dp.grad_k = bk;
+  plan->dp.grad_split = bs;
+  PET_CK(zero_accumulators(plan, plan->d_img, st));  // leave the transposed accumulator clear
+  PET_CK(cudaStreamSynchronize(st));
+  if (planes_per_thread) *planes_per_thread = bk;
+  if (parts) *parts = bs;
+  return PET_OK;
+}

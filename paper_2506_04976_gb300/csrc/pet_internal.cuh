@@ -40,6 +40,8 @@ struct DevPlan {
   float tof_erfc_amax;  // erfc(amax)
   float tof_half_norm;  // 1 / (2 erf(amax))
   int *err;             // device error word (bit 0: infeasible ybar)
+  int grad_k;           // fused gradient: planes per thread (non-TOF; 0 = heuristic)
+  int grad_split;       // fused gradient: parts per LOR (0 = heuristic)
 };
 
 // Per-view data for the voxel-driven (deterministic) backprojector: fb0 is affine in
@@ -180,6 +182,7 @@ cudaError_t launch_grad(const DevPlan &P, int subset, const int *subset_dev, con
                         const float *xT, float *g, float *gT, double *kl_part, int mode,
                         int *nblocks_out, cudaStream_t st);
 int grad_blocks(const DevPlan &P, int max_views);
+cudaError_t launch_fill(float *p, size_t n, float v, cudaStream_t st);
 cudaError_t launch_transpose(const float *src, float *dst, int nx, int ny, int nz, int to_xfast,
                              int accumulate, cudaStream_t st);
 cudaError_t launch_mult(const DevPlan &P, const float *mu, const float *muT, const float *sens,

@@ -4,6 +4,7 @@
 // sensitivity).  One thread owns one LOR; adjacent threads own adjacent radial bins of
 // the same view and plane, so their samples at a given plane touch adjacent voxels of
 // the driving-frame image.
+#include <algorithm>
 #include <atomic>
 
 #include "pet_internal.cuh"
@@ -272,6 +273,179 @@ __global__ void __launch_bounds__(kBlock) k_grad(DevPlan P, int subset, const in
   if (kl_part) block_sum_store(kl, kl_part + blockIdx.x);
 }
 
+// Multi-plane fused subset gradient (non-TOF): each thread owns K consecutive planes of
+// one (view, radial bin).  The in-plane sample position (fb, its floor and weight) is
+// shared by the K LORs, each plane adds only its axial coordinate; the K accumulation
+// chains are independent, which keeps more loads in flight per thread.  Parts (SPLIT)
+// interleave the planes i exactly as in k_grad.  Per LOR the arithmetic is that of
+// k_grad<1, SPLIT>.
+template <int K, int SPLIT>
+__global__ void __launch_bounds__(kBlock) k_grad_mp(DevPlan P, int subset, const int *subset_dev,
+                                                    const float *__restrict__ x, const float *__restrict__ xT,
+                                                    float *__restrict__ g, float *__restrict__ gT,
+                                                    double *__restrict__ kl_part, int mode) {
+  constexpr int LPB = kBlock / SPLIT;
+  __shared__ float xs[SPLIT > 1 ? SPLIT : 1][SPLIT > 1 ? LPB : 1][K];
+  if (subset_dev) subset = *subset_dev;
+  const int part = threadIdx.x / LPB;
+  const int tl = threadIdx.x % LPB;
+  const int nsub = subset < 0 ? 1 : P.nsub;
+  const int s0 = subset < 0 ? 0 : subset;
+  const int nv = (P.nview - s0 + nsub - 1) / nsub;
+  const int npg = (P.nplane + K - 1) / K;
+  const long long u = (long long)blockIdx.x * LPB + tl;
+  const bool ok = u < (long long)nv * npg * P.nrad;
+  int v = 0, r = 0, p0 = 0;
+  if (ok) {
+    r = (int)(u % P.nrad);
+    const long long t = u / P.nrad;
+    p0 = (int)(t % npg) * K;
+    v = s0 + (int)(t / npg) * nsub;
+  }
+  // shared in-plane geometry (lor_setup for the K planes at once)
+  const float4 vw = __ldg(&P.view[v]);
+  const float4 vr = __ldg(&P.vr[v * P.nrad + r]);
+  const bool xdrive = vw.x != 0.f;
+  const float dfb = vw.y, dau = vw.z, fb0 = vr.x, t0b = vr.y, inv2h = vr.z;
+  const float g1 = dau * inv2h, g2 = t0b * inv2h;
+  const int Na = xdrive ? P.nx : P.ny;
+  const int Nb = xdrive ? P.ny : P.nx;
+  const int plane = Na * Nb;
+  float fz0[K], dfz[K], Lk[K];
+  bool pv[K];
+  float lo_b = 0.f, hi_b = (float)(Na - 1);
+  clip_range(fb0, dfb, -1.f, (float)Nb, lo_b, hi_b);
+  float lo = 1e30f, hi = -1e30f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int p = p0 + k;
+    pv[k] = ok && p < P.nplane;
+    const float4 pl = __ldg(&P.plane[pv[k] ? p : 0]);
+    dfz[k] = g1 * pl.y;
+    fz0[k] = fmaf(g2, pl.y, pl.x);
+    const float kk = pl.z * inv2h;
+    Lk[k] = fabsf(dau) * sqrtf(fmaf(kk, kk, 1.f));
+    float lk = lo_b, hk = hi_b;
+    clip_range(fz0[k], dfz[k], -1.f, (float)P.nz, lk, hk);
+    if (pv[k] && lk <= hk) { lo = fminf(lo, lk); hi = fmaxf(hi, hk); }
+  }
+  Lor L = {};
+  if (lo <= hi) {
+    lo = fmaxf(lo, -2.f);
+    hi = fminf(hi, (float)Na + 1.f);
+    L.i0 = max(0, (int)floorf(lo) - 1);
+    L.i1 = min(Na - 1, (int)ceilf(hi) + 1);
+  } else {
+    L.i0 = 1;
+    L.i1 = 0;
+  }
+  warp_uniform_range(L, ok);
+  const float *img = xdrive ? xT : x;
+  float acc[K], cmp[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) { acc[k] = 0.f; cmp[k] = 0.f; }
+  if (mode != MODE_SENS) {
+    for (int i = L.i0 + part; i <= L.i1; i += SPLIT) {
+      if (!ok || i >= Na) continue;
+      const float fb = fmaf((float)i, dfb, fb0);
+      const float fbf = floorf(fb);
+      const int ib = (int)fbf;
+      const float wb = fb - fbf;
+      const bool b0 = (unsigned)ib < (unsigned)Nb;
+      const bool b1 = (unsigned)(ib + 1) < (unsigned)Nb && wb != 0.f;
+      const int row = i * Nb + ib;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float fz = fmaf((float)i, dfz[k], fz0[k]);
+        const float fzf = floorf(fz);
+        const int iz = (int)fzf;
+        const float wz = fz - fzf;
+        const bool z0 = pv[k] && (unsigned)iz < (unsigned)P.nz;
+        const bool z1 = pv[k] && (unsigned)(iz + 1) < (unsigned)P.nz && wz != 0.f;
+        const int base = iz * plane + row;
+        const float v00 = (z0 && b0) ? __ldg(img + base) : 0.f;
+        const float v01 = (z0 && b1) ? __ldg(img + base + 1) : 0.f;
+        const float v10 = (z1 && b0) ? __ldg(img + base + plane) : 0.f;
+        const float v11 = (z1 && b1) ? __ldg(img + base + plane + 1) : 0.f;
+        const float val = (1.f - wz) * ((1.f - wb) * v00 + wb * v01) + wz * ((1.f - wb) * v10 + wb * v11);
+        kahan_add(acc[k], cmp[k], val);
+      }
+    }
+    if (SPLIT > 1) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) xs[part][tl][k] = acc[k];
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        float t = xs[0][tl][k];
+#pragma unroll
+        for (int j = 1; j < SPLIT; ++j) t += xs[j][tl][k];
+        acc[k] = t;
+      }
+    }
+  }
+  double kl = 0.0;
+  float q[K];
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    q[k] = 0.f;
+    if (!pv[k]) continue;
+    const size_t lor = ((size_t)v * P.nplane + p0 + k) * P.nrad + r;
+    const float mL = __ldg(&P.m[lor]) * Lk[k];
+    if (mode == MODE_SENS) {
+      q[k] = mL;
+    } else {
+      const float ybar = fmaf(mL, acc[k], __ldg(&P.r[lor]));
+      const float yb = load_y(P, lor);
+      const bool count = kl_part && part == 0;
+      if (!(ybar > 0.f)) {
+        if (yb > 0.f) atomicOr(P.err, 1);
+        q[k] = (mode == MODE_GRAD && yb == 0.f) ? mL : 0.f;
+        if (count && yb == 0.f) kl += (double)fmaxf(ybar, 0.f);
+      } else {
+        if (mode == MODE_GRAD) q[k] = mL * (1.f - yb / ybar);
+        else if (mode == MODE_EM) q[k] = mL * (yb / ybar);
+        if (count) {
+          const double db = ybar, dy = yb;
+          kl += (yb > 0.f) ? (db - dy + dy * log(dy / db)) : db;
+        }
+      }
+    }
+    any |= q[k] != 0.f;
+  }
+  if (mode != MODE_OBJ) {
+    float *out = xdrive ? gT : g;
+    for (int i = L.i0 + part; i <= L.i1; i += SPLIT) {
+      if (!any || i >= Na) continue;
+      const float fb = fmaf((float)i, dfb, fb0);
+      const float fbf = floorf(fb);
+      const int ib = (int)fbf;
+      const float wb = fb - fbf;
+      const bool b0 = (unsigned)ib < (unsigned)Nb;
+      const bool b1 = (unsigned)(ib + 1) < (unsigned)Nb && wb != 0.f;
+      const int row = i * Nb + ib;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (q[k] == 0.f) continue;
+        const float fz = fmaf((float)i, dfz[k], fz0[k]);
+        const float fzf = floorf(fz);
+        const int iz = (int)fzf;
+        const float wz = fz - fzf;
+        const bool z0 = (unsigned)iz < (unsigned)P.nz;
+        const bool z1 = (unsigned)(iz + 1) < (unsigned)P.nz && wz != 0.f;
+        const int base = iz * plane + row;
+        const float a0 = (1.f - wz) * q[k], a1 = wz * q[k];
+        if (z0 && b0) atomicAdd(out + base, (1.f - wb) * a0);
+        if (z0 && b1) atomicAdd(out + base + 1, wb * a0);
+        if (z1 && b0) atomicAdd(out + base + plane, (1.f - wb) * a1);
+        if (z1 && b1) atomicAdd(out + base + plane + 1, wb * a1);
+      }
+    }
+  }
+  if (kl_part) block_sum_store(kl, kl_part + blockIdx.x);
+}
+
 // m = sens * exp(-P mu) for every LOR (non-TOF forward of the attenuation image).
 __global__ void __launch_bounds__(kBlock) k_mult(DevPlan P, const float *__restrict__ mu,
                                                  const float *__restrict__ muT,
@@ -427,7 +601,17 @@ __global__ void __launch_bounds__(kBlock) k_ratio(DevPlan P, int subset, const f
   if (kl_part) block_sum_store(kl, kl_part + blockIdx.x);
 }
 
+__global__ void k_fill(float *__restrict__ p, size_t n, float v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
 // ----------------------------------------------------------------- launchers
+cudaError_t launch_fill(float *p, size_t n, float v, cudaStream_t st) {
+  note_launch();
+  k_fill<<<(unsigned)std::min<size_t>(2432, (n + 255) / 256), 256, 0, st>>>(p, n, v);
+  return cudaGetLastError();
+}
+
 static int views_in(const DevPlan &P, int subset) {
   if (subset < 0) return P.nview;
   return (P.nview - subset + P.nsub - 1) / P.nsub;
@@ -473,11 +657,8 @@ static int split_for(long long nlor) {
   return 4;
 }
 
-int grad_blocks(const DevPlan &P, int max_views) {
-  const long long nlor = (long long)max_views * P.nplane * P.nrad;
-  const int lpb = kBlock / split_for(nlor);
-  return (int)((nlor + lpb - 1) / lpb);
-}
+int grad_blocks_for(const DevPlan &P, int nv);
+int grad_blocks(const DevPlan &P, int max_views) { return grad_blocks_for(P, max_views); }
 
 #define PET_GRAD_LAUNCH(SPLIT)                                                                  \
   do {                                                                                         \
@@ -488,20 +669,55 @@ int grad_blocks(const DevPlan &P, int max_views) {
     else k_grad<32, SPLIT><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);           \
   } while (0)
 
+static int views_for_launch(const DevPlan &P, int subset, const int *subset_dev) {
+  return subset_dev ? (P.nview + P.nsub - 1) / P.nsub : views_in(P, subset);
+}
+
+// Launch shape of the fused gradient: planes per thread (non-TOF only) and parts per
+// LOR.  P.grad_k / P.grad_split hold the autotuner's choice (0: heuristic).
+static void grad_shape(const DevPlan &P, long long nlor, int &K, int &split) {
+  K = (P.T <= 1 && P.grad_k > 0) ? P.grad_k : 1;
+  split = P.grad_split > 0 ? P.grad_split : split_for(nlor);
+}
+
+int grad_blocks_for(const DevPlan &P, int nv) {
+  const long long nlor = (long long)nv * P.nplane * P.nrad;
+  int K, split;
+  grad_shape(P, nlor, K, split);
+  const long long units = (long long)nv * ((P.nplane + K - 1) / K) * P.nrad;
+  const int lpb = kBlock / split;
+  return (int)((units + lpb - 1) / lpb);
+}
+
+#define PET_GRAD_MP(KK, SP) k_grad_mp<KK, SP><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode)
+
 cudaError_t launch_grad(const DevPlan &P, int subset, const int *subset_dev, const float *x,
                         const float *xT, float *g, float *gT, double *kl_part, int mode,
                         int *nblocks_out, cudaStream_t st) {
   // with a device-side subset index the grid covers the largest subset
-  const int nv = subset_dev ? (P.nview + P.nsub - 1) / P.nsub : views_in(P, subset);
+  const int nv = views_for_launch(P, subset, subset_dev);
   const long long nlor = (long long)nv * P.nplane * P.nrad;
-  const int split = split_for(nlor);
-  const unsigned grid = (unsigned)grad_blocks(P, nv);
+  int K, split;
+  grad_shape(P, nlor, K, split);
+  const unsigned grid = (unsigned)grad_blocks_for(P, nv);
   if (nblocks_out) *nblocks_out = (int)grid;
   if (grid == 0) return cudaSuccess;
   note_launch();
-  if (split == 4) PET_GRAD_LAUNCH(4);
-  else if (split == 2) PET_GRAD_LAUNCH(2);
-  else PET_GRAD_LAUNCH(1);
+  if (K == 4) {
+    if (split == 4) PET_GRAD_MP(4, 4);
+    else if (split == 2) PET_GRAD_MP(4, 2);
+    else PET_GRAD_MP(4, 1);
+  } else if (K == 2) {
+    if (split == 4) PET_GRAD_MP(2, 4);
+    else if (split == 2) PET_GRAD_MP(2, 2);
+    else PET_GRAD_MP(2, 1);
+  } else if (split == 4) {
+    PET_GRAD_LAUNCH(4);
+  } else if (split == 2) {
+    PET_GRAD_LAUNCH(2);
+  } else {
+    PET_GRAD_LAUNCH(1);
+  }
   return cudaGetLastError();
 }
 

@@ -302,3 +302,41 @@ def test_y_zero_and_zero_image():
     views = O.subset_views(c.g["nview"], c.n, 0)
     ref = (c.m[views][..., None] * O.project(c.G, c.x, views)).sum() + c.p["r"][views].astype(np.float64).sum()
     assert abs(float(obj) - ref) <= 1e-5 * ref
+
+
+@pytest.mark.parametrize("key", ["c1", "3d", "tof"])
+@pytest.mark.parametrize("shape", [(1, 1), (1, 2), (1, 4), (2, 1), (2, 4), (4, 1), (4, 2), (4, 4)])
+def test_grad_launch_shapes(key, shape):
+    """Every launch shape of the fused gradient (planes per thread x parts per LOR)
+    gives the oracle's subset objective and gradient."""
+    c = case(key)
+    k, parts = shape
+    if k > 1 and c.plan.T > 1:
+        pytest.skip("planes per thread > 1 is non-TOF only")
+    c.plan.set_grad_shape(k, parts)
+    try:
+        s = 3
+        obj, g = c.plan.objective_grad(c.xt, s)
+        val, gd = O.data_grad(c.G, c.n, s, c.x, c.m, c.p["r"], c.p["y"])
+        scale = O.sensitivity(c.G, c.n, s, c.m)
+        d = np.abs(g.cpu().numpy() - gd)
+        assert np.linalg.norm(d) <= 1e-5 * np.linalg.norm(scale)
+        assert d.max() <= 1e-4 * scale.max()
+        assert abs(float(obj) - val) <= 1e-5 * abs(val)
+        # EM mode shares the kernel
+        x = c.xt.clone()
+        c.plan.em_update(x, 2)
+        _close(x.cpu().numpy(), O.em_update(c.G, c.n, 2, c.m, c.p["r"], c.p["y"], c.x))
+    finally:
+        c.plan.set_grad_shape(0, 0)
+
+
+def test_autotune_keeps_parity():
+    c = case("3d")
+    k, parts = c.plan.autotune()
+    assert k in (1, 2, 4) and parts in (1, 2, 4)
+    _, g = c.plan.objective_grad(c.xt, 1)
+    _, gd = O.data_grad(c.G, c.n, 1, c.x, c.m, c.p["r"], c.p["y"])
+    scale = O.sensitivity(c.G, c.n, 1, c.m)
+    assert np.linalg.norm(g.cpu().numpy() - gd) <= 1e-5 * np.linalg.norm(scale)
+    c.plan.set_grad_shape(0, 0)
