@@ -42,9 +42,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-nrmse", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--mode", default="step", choices=["step", "grad"],
                     help="grad: only the fused subset-gradient op, for profiler captures")
+    ap.add_argument("--shape", default="auto",
+                    help="grad mode: 'auto' (autotuner) or 'K,S' planes per thread, parts per LOR")
     return ap.parse_args()
 
 
@@ -70,14 +73,15 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_tag):
+def ncu_traffic(kernel_tag, kernel_name):
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if
-    the kernel source is unchanged since the counters were taken; else None."""
+    it profiled the same kernel variant and the kernel source is unchanged since the
+    counters were taken; else None."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    if d.get("source_hash") != source_hash():
+    if d.get("source_hash") != source_hash() or d.get("kernel") != kernel_name:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -198,6 +202,53 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def time_to_nrmse(pet, dev, config, seed=0, threshold=0.01, max_epochs=3000):
+    """GPU wall time from the start of the OSEM initialisation (Sec. 3.1) to the first
+    epoch whose NRMSE (c19 reading) against the oracle's converged image is below the
+    threshold, for the graph form and the plain form (one launch per kernel).  Returns
+    None when no reference image has been written for this configuration."""
+    import torch
+    ref_path = os.path.join(ROOT, "tests", "golden", f"ref_{config}_seed{seed}.npz")
+    if not os.path.exists(ref_path):
+        return None
+    from paper_2506_04976_gb300 import synth
+    ref = np.load(ref_path)
+    p = synth.make_problem(config, seed)
+    n = p["nsub"]
+    plan = pet.Plan(p["geom"], n)
+    y = p["y"].view(np.int16) if p["y"].dtype == np.uint16 else p["y"].astype(np.int32)
+    plan.set_data(torch.from_numpy(y).to(dev), torch.from_numpy(p["r"]).to(dev),
+                  torch.from_numpy(p["mu"].astype(np.float32)).to(dev),
+                  torch.from_numpy(p["sens"].astype(np.float32)).to(dev))
+    plan.autotune()
+    xref = torch.from_numpy(ref["x"]).to(dev)
+    mask = torch.from_numpy(p["mask"]).to(dev)
+    bg = torch.from_numpy(p["bg"]).to(dev)
+    out = {"reference_kkt": float(ref["kkt"]), "threshold": threshold}
+    for form in ("graph", "plain"):
+        solver = pet.Solver(plan, algo=pet.SVRG, omega=2, step_rule=pet.STEP_VANISH, tau0=1.0, eta=0.02,
+                            precond_kind=1, pc_iters=(0, n, 2 * n), beta=p["beta"], gamma=p["gamma"],
+                            eps=p["eps"], seed=77, use_graph=(form == "graph"))
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        x = torch.ones(plan.img_shape, device=dev)
+        for s in range(n):
+            plan.em_update(x, s)
+        solver.set_image(x)
+        reached, val = None, None
+        for e in range(1, max_epochs + 1):
+            solver.run(n)
+            val = float(pet.nrmse(solver.image(), xref, mask, bg))
+            if val < threshold:
+                reached = e
+                break
+        b.record()
+        torch.cuda.synchronize()
+        out[form] = {"seconds": a.elapsed_time(b) / 1e3, "epochs": reached, "final_nrmse": val}
+    return out
+
+
 def run_grad_only(args, pet, dev):
     """Subset gradients only (objective_grad on successive subsets), for ncu captures."""
     import torch
@@ -206,7 +257,11 @@ def run_grad_only(args, pet, dev):
     plan.set_data(torch.from_numpy(p["y"].view(np.int16)).to(dev), torch.from_numpy(p["r"]).to(dev),
                   torch.from_numpy(p["mu"].astype(np.float32)).to(dev),
                   torch.from_numpy(p["sens"].astype(np.float32)).to(dev))
-    plan.autotune()
+    if args.shape == "auto":
+        plan.autotune()
+    else:
+        k, sp = (int(v) for v in args.shape.split(","))
+        plan.set_grad_shape(k, sp)
     x = torch.from_numpy(np.maximum(p["x_true"], 0.05 * p["x_true"].max()).astype(np.float32)).to(dev)
     gbuf = torch.empty_like(x)
     for i in range(args.warmup):
@@ -342,9 +397,10 @@ def main():
     kavg = kern_ms / max(kern_n, 1)
     abytes = algorithmic_bytes_per_grad(p)
     achieved = abytes / (kavg * 1e-3) / 1e9
+    kname = f"k_grad_mp<{shape[0]},{shape[1]}>" if shape[0] > 1 else f"k_grad<1,{shape[1]}>"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": ncu_traffic("k_grad_c2"),
-                "kernel": "k_grad<1> (fused forward, KL ratio, backprojection of one subset)",
+                "frac": achieved / peak, "traffic": ncu_traffic("k_grad_c2", kname),
+                "kernel": kname + " (fused forward, KL ratio, backprojection of one subset)",
                 "kernel_ms": kavg, "launches_timed": kern_n, "algorithmic_bytes": abytes,
                 "peak_kind": f"hbm_gbs {peak_kind}", "launch_shape": {"planes_per_thread": shape[0],
                                                                       "parts_per_lor": shape[1]}}
@@ -354,6 +410,12 @@ def main():
         cpu = {"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{len(times)} full-size c2 subset gradients (fwd+back+RDP), FP64, 1 thread"}
     clocks = clk.summary()
+    nrmse_times = {}
+    if not args.no_nrmse:
+        for cfg in ("c1", "c2"):
+            t = time_to_nrmse(pet, dev, cfg)
+            if t is not None:
+                nrmse_times[cfg] = t
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
@@ -362,7 +424,7 @@ def main():
                    "iterations = 62 subset gradients", "l2": "flushed between steps (256 MB write)",
                    "graph": "one CUDA graph per epoch", "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clocks, "wall_s_timed": wall,
+        "clocks": clocks, "wall_s_timed": wall, "time_to_1pct_nrmse": nrmse_times or None,
     }
     print(json.dumps(line), flush=True)
     if pg:

@@ -45,7 +45,49 @@ __device__ __forceinline__ double block_sum_d(double v) {
   return s;  // valid in thread 0
 }
 
-template <bool KAPPA, bool VAL>
+// Per-voxel RDP sums over the 26 neighbours held in the shared-memory planes.  BOUND
+// enables the image-boundary checks (interior tiles skip them).
+template <bool KAPPA, bool WG, bool WH, bool VAL, bool BOUND>
+__device__ __forceinline__ void rdp_voxel(const RdpArgs &a, const float (*sx)[RDP_TY + 2][RDP_TX + 2],
+                                          const float (*sk)[RDP_TY + 2][RDP_TX + 2], int z, int gx, int gy,
+                                          int tx, int ty, float &gsum, float &hsum, float &vs) {
+  const int sc = (z + 3) % 3;
+  const float xi = sx[sc][ty + 1][tx + 1];
+  const float ki = KAPPA ? sk[sc][ty + 1][tx + 1] : 1.f;
+#pragma unroll
+  for (int oz = -1; oz <= 1; ++oz) {
+    const int jz = z + oz;
+    if (BOUND && (jz < 0 || jz >= a.nz)) continue;
+    const int sl = (jz + 3) % 3;
+#pragma unroll
+    for (int oy = -1; oy <= 1; ++oy) {
+      if (BOUND && (gy + oy < 0 || gy + oy >= a.ny)) continue;
+#pragma unroll
+      for (int ox = -1; ox <= 1; ++ox) {
+        if (ox == 0 && oy == 0 && oz == 0) continue;
+        if (BOUND && (gx + ox < 0 || gx + ox >= a.nx)) continue;
+        constexpr int widx[8] = {-1, 0, 1, 3, 2, 4, 5, 6};
+        const int code = (ox != 0 ? 1 : 0) + (oy != 0 ? 2 : 0) + (oz != 0 ? 4 : 0);
+        float w = a.w[widx[code]];
+        const float xj = sx[sl][ty + 1 + oy][tx + 1 + ox];
+        if (KAPPA) w *= ki * sk[sl][ty + 1 + oy][tx + 1 + ox];
+        const float d = xi - xj;
+        const float ad = fabsf(d);
+        const float phi = (xi + xj) + a.gamma * ad + a.eps;
+        const float inv = __fdividef(1.f, phi);
+        const float inv2 = inv * inv;
+        if (WG) gsum = fmaf(w * d * ((2.f * phi - d) - a.gamma * ad), inv2, gsum);
+        if (WH) {
+          const float e2 = fmaf(2.f, xj, a.eps);
+          hsum = fmaf(2.f * w * e2 * e2, inv2 * inv, hsum);
+        }
+        if (VAL) vs = fmaf(w * d * d, inv, vs);
+      }
+    }
+  }
+}
+
+template <bool KAPPA, bool WG, bool WH, bool VAL>
 __global__ void __launch_bounds__(RDP_TX * RDP_TY) k_rdp(RdpArgs a, const float *__restrict__ x,
                                                           float *__restrict__ grad, float *__restrict__ hdiag,
                                                           double *__restrict__ val_part, int accumulate) {
@@ -57,6 +99,8 @@ __global__ void __launch_bounds__(RDP_TX * RDP_TY) k_rdp(RdpArgs a, const float 
   const int x0 = bx * RDP_TX, y0 = by * RDP_TY;
   const int z0 = bz * RDP_ZCH, z1 = min(a.nz, z0 + RDP_ZCH);
   const int nxy = a.nx * a.ny;
+  // the tile and its in-plane halo lie inside the image
+  const bool inner_xy = x0 >= 1 && x0 + RDP_TX < a.nx && y0 >= 1 && y0 + RDP_TY < a.ny;
 
   auto load_plane = [&](int z) {
     const int slot = (z + 3) % 3;
@@ -82,42 +126,14 @@ __global__ void __launch_bounds__(RDP_TX * RDP_TY) k_rdp(RdpArgs a, const float 
     load_plane(z + 1);
     __syncthreads();
     if (gx < a.nx && gy < a.ny) {
-      const int sc = (z + 3) % 3;
-      const float xi = sx[sc][ty + 1][tx + 1];
-      const float ki = KAPPA ? sk[sc][ty + 1][tx + 1] : 1.f;
       float gsum = 0.f, hsum = 0.f, vs = 0.f;
-#pragma unroll
-      for (int oz = -1; oz <= 1; ++oz) {
-        const int jz = z + oz;
-        if (jz < 0 || jz >= a.nz) continue;
-        const int sl = (jz + 3) % 3;
-#pragma unroll
-        for (int oy = -1; oy <= 1; ++oy) {
-          if (gy + oy < 0 || gy + oy >= a.ny) continue;
-#pragma unroll
-          for (int ox = -1; ox <= 1; ++ox) {
-            if (ox == 0 && oy == 0 && oz == 0) continue;
-            if (gx + ox < 0 || gx + ox >= a.nx) continue;
-            constexpr int widx[8] = {-1, 0, 1, 3, 2, 4, 5, 6};
-            const int code = (ox != 0 ? 1 : 0) + (oy != 0 ? 2 : 0) + (oz != 0 ? 4 : 0);
-            float w = a.w[widx[code]];
-            const float xj = sx[sl][ty + 1 + oy][tx + 1 + ox];
-            if (KAPPA) w *= ki * sk[sl][ty + 1 + oy][tx + 1 + ox];
-            const float d = xi - xj;
-            const float ad = fabsf(d);
-            const float phi = (xi + xj) + a.gamma * ad + a.eps;
-            const float inv = __fdividef(1.f, phi);
-            const float inv2 = inv * inv;
-            gsum = fmaf(w * d * ((2.f * phi - d) - a.gamma * ad), inv2, gsum);
-            const float e2 = fmaf(2.f, xj, a.eps);
-            hsum = fmaf(2.f * w * e2 * e2, inv2 * inv, hsum);
-            if (VAL) vs = fmaf(w * d * d, inv, vs);
-          }
-        }
-      }
+      if (inner_xy && z >= 1 && z + 1 < a.nz)
+        rdp_voxel<KAPPA, WG, WH, VAL, false>(a, sx, sk, z, gx, gy, tx, ty, gsum, hsum, vs);
+      else
+        rdp_voxel<KAPPA, WG, WH, VAL, true>(a, sx, sk, z, gx, gy, tx, ty, gsum, hsum, vs);
       const size_t gi = (size_t)z * nxy + (size_t)gy * a.nx + gx;
-      if (grad) grad[gi] = accumulate ? fmaf(a.scale, gsum, grad[gi]) : a.scale * gsum;
-      if (hdiag) hdiag[gi] = a.scale * hsum;
+      if (WG) grad[gi] = accumulate ? fmaf(a.scale, gsum, grad[gi]) : a.scale * gsum;
+      if (WH) hdiag[gi] = a.scale * hsum;
       if (VAL) vsum += 0.5 * (double)vs;
     }
     __syncthreads();
@@ -128,19 +144,31 @@ __global__ void __launch_bounds__(RDP_TX * RDP_TY) k_rdp(RdpArgs a, const float 
   }
 }
 
+template <bool KAPPA>
+static void rdp_dispatch(const RdpArgs &a, int nb, dim3 block, const float *x, float *grad, float *hdiag,
+                         double *val_part, int accumulate, cudaStream_t st) {
+  const int code = (grad ? 1 : 0) | (hdiag ? 2 : 0) | (val_part ? 4 : 0);
+  switch (code) {
+    case 1: k_rdp<KAPPA, true, false, false><<<nb, block, 0, st>>>(a, x, grad, hdiag, val_part, accumulate); break;
+    case 2: k_rdp<KAPPA, false, true, false><<<nb, block, 0, st>>>(a, x, grad, hdiag, val_part, accumulate); break;
+    case 3: k_rdp<KAPPA, true, true, false><<<nb, block, 0, st>>>(a, x, grad, hdiag, val_part, accumulate); break;
+    case 4: k_rdp<KAPPA, false, false, true><<<nb, block, 0, st>>>(a, x, grad, hdiag, val_part, accumulate); break;
+    case 5: k_rdp<KAPPA, true, false, true><<<nb, block, 0, st>>>(a, x, grad, hdiag, val_part, accumulate); break;
+    case 6: k_rdp<KAPPA, false, true, true><<<nb, block, 0, st>>>(a, x, grad, hdiag, val_part, accumulate); break;
+    case 7: k_rdp<KAPPA, true, true, true><<<nb, block, 0, st>>>(a, x, grad, hdiag, val_part, accumulate); break;
+    default: break;
+  }
+}
+
 cudaError_t launch_rdp(const RdpArgs &a, const float *x, float *grad, float *hdiag,
                        double *val_part, int accumulate, int *nblocks_out, cudaStream_t st) {
   const int nb = rdp_blocks(a.nx, a.ny, a.nz);
   if (nblocks_out) *nblocks_out = nb;
+  if (!grad && !hdiag && !val_part) return cudaSuccess;
   dim3 block(RDP_TX, RDP_TY);
   note_launch();
-  if (a.kappa) {
-    if (val_part) k_rdp<true, true><<<nb, block, 0, st>>>(a, x, grad, hdiag, val_part, accumulate);
-    else k_rdp<true, false><<<nb, block, 0, st>>>(a, x, grad, hdiag, val_part, accumulate);
-  } else {
-    if (val_part) k_rdp<false, true><<<nb, block, 0, st>>>(a, x, grad, hdiag, val_part, accumulate);
-    else k_rdp<false, false><<<nb, block, 0, st>>>(a, x, grad, hdiag, val_part, accumulate);
-  }
+  if (a.kappa) rdp_dispatch<true>(a, nb, block, x, grad, hdiag, val_part, accumulate, st);
+  else rdp_dispatch<false>(a, nb, block, x, grad, hdiag, val_part, accumulate, st);
   return cudaGetLastError();
 }
 
