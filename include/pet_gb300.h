@@ -144,6 +144,14 @@ pet_status pet_back(pet_plan *plan, int subset, const float *q, float *g, int de
 pet_status pet_objective_grad(pet_plan *plan, int subset, const float *x, float *g, double *obj,
                               const pet_rdp_params *prior, int flags, void *stream);
 
+/* KL ratio from a stored forward projection ax = A_s x (compact subset layout, e.g. from
+ * pet_forward): q = 1 - y/(ax + r) (em = 0; the derivative of d(s, y) in s, Sec. 1.2) or
+ * q = y/(ax + r) (em = 1), and obj (device double, may be NULL) = sum of d(ax + r, y)
+ * over the subset in FP64.  q may be NULL.  g = pet_back(q) then completes the data
+ * gradient of eq. 5 without projecting again. */
+pet_status pet_ratio(pet_plan *plan, int subset, const float *ax, float *q, double *obj, int em,
+                     void *stream);
+
 /* One OSEM sub-iteration on subset s (MLEM for nsubsets = 1), in place:
  * x <- x / (A_s^T 1) * A_s^T (y_s / (A_s x + r_s)); voxels with A_s^T 1 = 0 keep their
  * value (Sec. 3.1 initialises runs with one OSEM epoch). */

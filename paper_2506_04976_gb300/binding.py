@@ -91,6 +91,7 @@ _sigs = {
     "pet_back": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, _vp]),
     "pet_objective_grad": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, C.POINTER(RdpParams), C.c_int, _vp]),
     "pet_em_update": (C.c_int, [_vp, C.c_int, _vp, _vp]),
+    "pet_ratio": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, C.c_int, _vp]),
     "pet_rdp": (C.c_int, [C.POINTER(RdpParams), _vp, _vp, _vp, _vp, C.c_int, _vp]),
     "pet_precond": (C.c_int, [_vp, _vp, _vp, C.c_float, C.c_float, _vp, _vp]),
     "pet_nrmse": (C.c_int, [_vp, _vp, _vp, _vp, C.c_size_t, _vp, _vp]),
@@ -246,6 +247,17 @@ class Plan:
                                     _ptr(obj, torch.float64) if obj is not None else None,
                                     rp, flags, _stream()), "pet_objective_grad")
         return obj, g
+
+    def ratio(self, ax, s=-1, want_q=True, want_obj=True):
+        """(sum of KL terms as a 0-d float64 tensor, q = 1 - y/(ax + r)) from ax = A_s x."""
+        shp = self.subset_shape(s) if s >= 0 else self.sino_shape
+        q = torch.empty(shp, device=ax.device) if want_q else None
+        obj = torch.zeros((), device=ax.device, dtype=torch.float64) if want_obj else None
+        _ck(_lib.pet_ratio(self._h, int(s), _ptr(ax, numel=int(np.prod(shp))),
+                           _ptr(q) if q is not None else None,
+                           _ptr(obj, torch.float64) if obj is not None else None, 0, _stream()),
+            "pet_ratio")
+        return obj, q
 
     def em_update(self, x, s):
         _ck(_lib.pet_em_update(self._h, int(s), _ptr(x, numel=self.N), _stream()), "pet_em_update")

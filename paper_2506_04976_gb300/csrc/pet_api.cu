@@ -417,3 +417,14 @@ extern "C" pet_status pet_plan_autotune(pet_plan *plan, void *stream, int *plane
   if (parts) *parts = bs;
   return PET_OK;
 }
+
+extern "C" pet_status pet_ratio(pet_plan *plan, int subset, const float *ax, float *q, double *obj, int em,
+                                void *stream) {
+  if (!plan || !ax || bad_subset(plan, subset) || (!q && !obj)) return PET_ERR_ARG;
+  if (!plan->has_data) return PET_ERR_STATE;
+  cudaStream_t st = S(stream);
+  const int nparts = ratio_blocks(plan->dp, subset);
+  PET_CK(launch_ratio(plan->dp, subset, ax, q, obj ? plan->d_part : nullptr, em ? MODE_EM : MODE_GRAD, st));
+  if (obj) PET_CK(launch_reduce_sum(plan->d_part, nparts, obj, 0, st));
+  return PET_OK;
+}
