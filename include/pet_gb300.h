@@ -237,6 +237,28 @@ pet_status pet_solver_run(pet_solver *s, long long niter, void *stream);
 long long pet_solver_taus(const pet_solver *s, double *taus, long long cap);
 long long pet_solver_iteration(const pet_solver *s);
 
+/* ---------------------------------------------------------------- batches */
+
+/* Many independent reconstructions advanced together (batched instances of uneven image
+ * and sinogram sizes, betas and count levels).  Each solver keeps its own plan, data,
+ * options and subset order; the batch runs every iteration as one launch per phase
+ * for all of them (fused subset gradient, RDP gradient, estimator + step + prox,
+ * accumulator clear) and captures iters_per_graph iterations in one CUDA graph,
+ * replayed after uploading each batch epoch's per-solver subsets and iteration indices.
+ * Iteration windows that contain a preconditioner update, and a final partial window,
+ * run per solver.  Requirements (else PET_ERR_UNSUPPORTED / PET_ERR_ARG): SGD or SAGA
+ * (all the same), non-TOF plans, no kappa image, no deterministic mode, distinct plans
+ * (a plan's scratch serves one solver at a time).  The solvers are borrowed. */
+typedef struct pet_batch pet_batch;
+pet_status pet_batch_create(pet_solver *const *solvers, int n, int iters_per_graph, pet_batch **out);
+void pet_batch_destroy(pet_batch *b);
+/* Runs niter iterations of every solver (each solver's iteration counter advances). */
+pet_status pet_batch_run(pet_batch *b, long long niter, void *stream);
+/* Launch shape of the batched fused gradient (as pet_plan_set_grad_shape) and its
+ * autotuner (times each shape on subset 0 of every solver; synchronises stream). */
+pet_status pet_batch_set_grad_shape(pet_batch *b, int planes_per_thread, int parts);
+pet_status pet_batch_autotune(pet_batch *b, void *stream, int *planes_per_thread, int *parts);
+
 /* Event timing of the fused subset-gradient kernel launched by the solver (the
  * dominant kernel of an iteration), recorded on the launching stream and inside
  * captured graphs.  Slots are unique within one SVRG outer loop (omega*n iterations)

@@ -104,6 +104,11 @@ _sigs = {
     "pet_solver_iteration": (C.c_longlong, [_vp]),
     "pet_solver_profile": (C.c_int, [_vp, C.c_int]),
     "pet_launch_count": (C.c_longlong, []),
+    "pet_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, C.POINTER(_vp)]),
+    "pet_batch_destroy": (None, [_vp]),
+    "pet_batch_run": (C.c_int, [_vp, C.c_longlong, _vp]),
+    "pet_batch_set_grad_shape": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "pet_batch_autotune": (C.c_int, [_vp, _vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "pet_solver_kernel_time": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
 }
 for _name, (_res, _args) in _sigs.items():
@@ -366,3 +371,31 @@ class Solver:
         buf = (C.c_double * max(n, 1))()
         c = _lib.pet_solver_taus(self._h, buf, n)
         return np.array(buf[:c])
+
+
+class Batch:
+    """Independent reconstructions advanced together (pet_batch_*)."""
+
+    def __init__(self, solvers, iters_per_graph=8):
+        self.solvers = list(solvers)
+        arr = (_vp * len(self.solvers))(*[sv._h for sv in self.solvers])
+        h = _vp()
+        _ck(_lib.pet_batch_create(arr, len(self.solvers), int(iters_per_graph), C.byref(h)), "pet_batch_create")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _lib.pet_batch_destroy(h)
+            self._h = None
+
+    def run(self, niter):
+        _ck(_lib.pet_batch_run(self._h, int(niter), _stream()), "pet_batch_run")
+
+    def set_grad_shape(self, planes_per_thread, parts):
+        _ck(_lib.pet_batch_set_grad_shape(self._h, int(planes_per_thread), int(parts)), "pet_batch_set_grad_shape")
+
+    def autotune(self):
+        k, sp = C.c_int(), C.c_int()
+        _ck(_lib.pet_batch_autotune(self._h, _stream(), C.byref(k), C.byref(sp)), "pet_batch_autotune")
+        return k.value, sp.value

@@ -88,14 +88,14 @@ __device__ __forceinline__ void rdp_voxel(const RdpArgs &a, const float (*sx)[RD
 }
 
 template <bool KAPPA, bool WG, bool WH, bool VAL>
-__global__ void __launch_bounds__(RDP_TX * RDP_TY) k_rdp(RdpArgs a, const float *__restrict__ x,
-                                                          float *__restrict__ grad, float *__restrict__ hdiag,
-                                                          double *__restrict__ val_part, int accumulate) {
+__device__ __forceinline__ void rdp_body(const RdpArgs &a, const float *__restrict__ x, float *__restrict__ grad,
+                                         float *__restrict__ hdiag, double *__restrict__ val_out, int accumulate,
+                                         int blk) {
   __shared__ float sx[3][RDP_TY + 2][RDP_TX + 2];
   __shared__ float sk[KAPPA ? 3 : 1][RDP_TY + 2][RDP_TX + 2];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * RDP_TX + tx;
   const int nbx = (a.nx + RDP_TX - 1) / RDP_TX, nby = (a.ny + RDP_TY - 1) / RDP_TY;
-  const int bx = blockIdx.x % nbx, by = (blockIdx.x / nbx) % nby, bz = blockIdx.x / (nbx * nby);
+  const int bx = blk % nbx, by = (blk / nbx) % nby, bz = blk / (nbx * nby);
   const int x0 = bx * RDP_TX, y0 = by * RDP_TY;
   const int z0 = bz * RDP_ZCH, z1 = min(a.nz, z0 + RDP_ZCH);
   const int nxy = a.nx * a.ny;
@@ -140,8 +140,45 @@ __global__ void __launch_bounds__(RDP_TX * RDP_TY) k_rdp(RdpArgs a, const float 
   }
   if (VAL) {
     const double s = block_sum_d(vsum * (double)a.scale);
-    if (tid == 0) val_part[blockIdx.x] = s;
+    if (tid == 0) *val_out = s;
   }
+}
+
+template <bool KAPPA, bool WG, bool WH, bool VAL>
+__global__ void __launch_bounds__(RDP_TX * RDP_TY) k_rdp(RdpArgs a, const float *__restrict__ x,
+                                                          float *__restrict__ grad, float *__restrict__ hdiag,
+                                                          double *__restrict__ val_part, int accumulate) {
+  rdp_body<KAPPA, WG, WH, VAL>(a, x, grad, hdiag, VAL ? val_part + blockIdx.x : nullptr, accumulate, blockIdx.x);
+}
+
+// Batched RDP gradient (no kappa, gradient only): blocks [begin[j], begin[j+1]) belong
+// to job j.
+__global__ void __launch_bounds__(RDP_TX * RDP_TY) k_rdp_batch(const RdpJob *__restrict__ jobs,
+                                                                const int *__restrict__ begin, int njobs) {
+  __shared__ int s_job;
+  __shared__ RdpJob sj;
+  const int tid = threadIdx.y * RDP_TX + threadIdx.x;
+  if (tid < 32) {
+    int job = 0;
+    for (int base = 0; base < njobs; base += 32) {
+      const int j = base + tid;
+      const unsigned m = __ballot_sync(0xffffffffu, j < njobs && __ldg(&begin[j]) <= (int)blockIdx.x);
+      job = base + __popc(m) - 1;
+      if (m != 0xffffffffu) break;
+    }
+    if (tid == 0) { s_job = job; sj = jobs[job]; }
+  }
+  __syncthreads();
+  rdp_body<false, true, false, false>(sj.a, sj.x, sj.grad, nullptr, nullptr, 0,
+                                      (int)blockIdx.x - __ldg(&begin[s_job]));
+}
+
+cudaError_t launch_rdp_batch(const RdpJob *jobs, const int *begin, int njobs, int total_blocks,
+                             cudaStream_t st) {
+  if (total_blocks <= 0) return cudaSuccess;
+  note_launch();
+  k_rdp_batch<<<total_blocks, dim3(RDP_TX, RDP_TY), 0, st>>>(jobs, begin, njobs);
+  return cudaGetLastError();
 }
 
 template <bool KAPPA>

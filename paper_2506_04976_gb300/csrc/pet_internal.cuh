@@ -183,6 +183,18 @@ cudaError_t launch_grad(const DevPlan &P, int subset, const int *subset_dev, con
                         int *nblocks_out, cudaStream_t st);
 int grad_blocks(const DevPlan &P, int max_views);
 cudaError_t launch_fill(float *p, size_t n, float v, cudaStream_t st);
+
+// One reconstruction of a batch, as seen by the batched fused-gradient kernel.
+struct GradJob {
+  DevPlan P;
+  const int *subset_dev;  // this job's subset for the iteration
+  const float *x, *xT;
+  float *g, *gT;
+};
+// Blocks [begin[j], begin[j+1]) belong to job j; all jobs use one launch shape (K, split).
+cudaError_t launch_grad_batch(const GradJob *jobs, const int *begin, int njobs, int total_blocks, int K,
+                              int split, cudaStream_t st);
+int grad_blocks_shape(const DevPlan &P, int nv, int K, int split);
 cudaError_t launch_transpose(const float *src, float *dst, int nx, int ny, int nz, int to_xfast,
                              int accumulate, cudaStream_t st);
 cudaError_t launch_mult(const DevPlan &P, const float *mu, const float *muT, const float *sens,
@@ -199,6 +211,13 @@ RdpArgs make_rdp_args(const pet_rdp_params &p);
 cudaError_t launch_rdp(const RdpArgs &a, const float *x, float *grad, float *hdiag,
                        double *val_part, int accumulate, int *nblocks_out, cudaStream_t st);
 int rdp_blocks(int nx, int ny, int nz);
+struct RdpJob {
+  RdpArgs a;
+  const float *x;
+  float *grad;
+};
+cudaError_t launch_rdp_batch(const RdpJob *jobs, const int *begin, int njobs, int total_blocks,
+                             cudaStream_t st);
 cudaError_t launch_reduce_sum(const double *part, int n, double *out, int accumulate,
                               cudaStream_t st);
 cudaError_t launch_max(const float *x, size_t n, float *part, float *out, cudaStream_t st);

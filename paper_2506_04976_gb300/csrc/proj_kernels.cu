@@ -280,20 +280,19 @@ __global__ void __launch_bounds__(kBlock) k_grad(DevPlan P, int subset, const in
 // interleave the planes i exactly as in k_grad.  Per LOR the arithmetic is that of
 // k_grad<1, SPLIT>.
 template <int K, int SPLIT>
-__global__ void __launch_bounds__(kBlock) k_grad_mp(DevPlan P, int subset, const int *subset_dev,
-                                                    const float *__restrict__ x, const float *__restrict__ xT,
-                                                    float *__restrict__ g, float *__restrict__ gT,
-                                                    double *__restrict__ kl_part, int mode) {
+__device__ __forceinline__ void grad_mp_body(const DevPlan &P, int subset, int blk,
+                                             const float *__restrict__ x, const float *__restrict__ xT,
+                                             float *__restrict__ g, float *__restrict__ gT,
+                                             double *__restrict__ kl_out, int mode) {
   constexpr int LPB = kBlock / SPLIT;
   __shared__ float xs[SPLIT > 1 ? SPLIT : 1][SPLIT > 1 ? LPB : 1][K];
-  if (subset_dev) subset = *subset_dev;
   const int part = threadIdx.x / LPB;
   const int tl = threadIdx.x % LPB;
   const int nsub = subset < 0 ? 1 : P.nsub;
   const int s0 = subset < 0 ? 0 : subset;
   const int nv = (P.nview - s0 + nsub - 1) / nsub;
   const int npg = (P.nplane + K - 1) / K;
-  const long long u = (long long)blockIdx.x * LPB + tl;
+  const long long u = (long long)blk * LPB + tl;
   const bool ok = u < (long long)nv * npg * P.nrad;
   int v = 0, r = 0, p0 = 0;
   if (ok) {
@@ -398,7 +397,7 @@ __global__ void __launch_bounds__(kBlock) k_grad_mp(DevPlan P, int subset, const
     } else {
       const float ybar = fmaf(mL, acc[k], __ldg(&P.r[lor]));
       const float yb = load_y(P, lor);
-      const bool count = kl_part && part == 0;
+      const bool count = kl_out && part == 0;
       if (!(ybar > 0.f)) {
         if (yb > 0.f) atomicOr(P.err, 1);
         q[k] = (mode == MODE_GRAD && yb == 0.f) ? mL : 0.f;
@@ -443,7 +442,69 @@ __global__ void __launch_bounds__(kBlock) k_grad_mp(DevPlan P, int subset, const
       }
     }
   }
-  if (kl_part) block_sum_store(kl, kl_part + blockIdx.x);
+  if (kl_out) block_sum_store(kl, kl_out);
+}
+
+template <int K, int SPLIT>
+__global__ void __launch_bounds__(kBlock) k_grad_mp(DevPlan P, int subset, const int *subset_dev,
+                                                    const float *__restrict__ x, const float *__restrict__ xT,
+                                                    float *__restrict__ g, float *__restrict__ gT,
+                                                    double *__restrict__ kl_part, int mode) {
+  if (subset_dev) subset = *subset_dev;
+  grad_mp_body<K, SPLIT>(P, subset, blockIdx.x, x, xT, g, gT, kl_part ? kl_part + blockIdx.x : nullptr, mode);
+}
+
+// Index of the job owning this block: jobs own consecutive block ranges starting at
+// begin[j] (begin[njobs] = total blocks).  One warp compares 32 offsets per step.
+__device__ __forceinline__ int find_job(const int *__restrict__ begin, int njobs) {
+  __shared__ int s_job;
+  if (threadIdx.x < 32) {
+    int job = 0;
+    for (int base = 0; base < njobs; base += 32) {
+      const int j = base + (int)threadIdx.x;
+      const bool le = j < njobs && __ldg(&begin[j]) <= (int)blockIdx.x;
+      const unsigned m = __ballot_sync(0xffffffffu, le);
+      job = base + __popc(m) - 1;
+      if (m != 0xffffffffu) break;
+    }
+    if (threadIdx.x == 0) s_job = job;
+  }
+  __syncthreads();
+  return s_job;
+}
+
+// Batched fused gradient: one launch covers the current subset of every job.
+template <int K, int SPLIT>
+__global__ void __launch_bounds__(kBlock) k_grad_mp_batch(const GradJob *__restrict__ jobs,
+                                                          const int *__restrict__ begin, int njobs, int mode) {
+  __shared__ GradJob sj;
+  const int j = find_job(begin, njobs);
+  if (threadIdx.x == 0) sj = jobs[j];
+  __syncthreads();
+  const int subset = *sj.subset_dev;
+  grad_mp_body<K, SPLIT>(sj.P, subset, (int)blockIdx.x - __ldg(&begin[j]), sj.x, sj.xT, sj.g, sj.gT, nullptr, mode);
+}
+
+cudaError_t launch_grad_batch(const GradJob *jobs, const int *begin, int njobs, int total_blocks, int K,
+                              int split, cudaStream_t st) {
+  if (total_blocks <= 0) return cudaSuccess;
+  note_launch();
+#define PET_GB(KK, SP) k_grad_mp_batch<KK, SP><<<total_blocks, kBlock, 0, st>>>(jobs, begin, njobs, MODE_GRAD)
+  if (K == 4) {
+    if (split == 4) PET_GB(4, 4); else if (split == 2) PET_GB(4, 2); else PET_GB(4, 1);
+  } else if (K == 2) {
+    if (split == 4) PET_GB(2, 4); else if (split == 2) PET_GB(2, 2); else PET_GB(2, 1);
+  } else {
+    if (split == 4) PET_GB(1, 4); else if (split == 2) PET_GB(1, 2); else PET_GB(1, 1);
+  }
+#undef PET_GB
+  return cudaGetLastError();
+}
+
+int grad_blocks_shape(const DevPlan &P, int nv, int K, int split) {
+  const long long units = (long long)nv * ((P.nplane + K - 1) / K) * P.nrad;
+  const int lpb = kBlock / split;
+  return (int)((units + lpb - 1) / lpb);
 }
 
 // m = sens * exp(-P mu) for every LOR (non-TOF forward of the attenuation image).

@@ -47,21 +47,23 @@ struct UpdArgs {
   float tau0, eta;
   SolverState *st;
   double *tau_log;   // indexed by k (may be NULL)
+  const int *subset_dev;     // if set, the subset is read from device memory (batches)
+  const long long *k_dev;    // if set, the iteration index is read from device memory
 };
 
-__device__ __forceinline__ float step_of(const UpdArgs &a) {
+__device__ __forceinline__ float step_of(const UpdArgs &a, long long ki) {
   double tau;
-  const double k = (double)a.k;
+  const double k = (double)ki;
   switch (a.rule) {
     case PET_STEP_CONST: tau = a.tau0; break;
     case PET_STEP_VANISH: tau = a.tau0 / (1.0 + a.eta * k / a.n); break;
     case PET_STEP_ALG1:
-      tau = a.k < 10 ? 3.0 : a.k < 100 ? 2.0 : a.k < 200 ? 1.5 : a.k < 300 ? 1.0 : 0.5;
+      tau = ki < 10 ? 3.0 : ki < 100 ? 2.0 : ki < 200 ? 1.5 : ki < 300 ? 1.0 : 0.5;
       break;
     case PET_STEP_BB: tau = a.st->have_bb ? a.st->tau_bb : a.tau0; break;
     default: {
       const double bb = a.st->have_bb ? a.st->tau_bb : a.tau0;
-      const double cap = a.k < 10 ? 3.0 : (a.k < 2LL * a.n ? 2.2 : 1.0);
+      const double cap = ki < 10 ? 3.0 : (ki < 2LL * a.n ? 2.2 : 1.0);
       tau = bb < cap ? bb : cap;
     }
   }
@@ -76,16 +78,19 @@ __device__ __forceinline__ float step_of(const UpdArgs &a) {
 // per block.  ALGO: 0 SGD, 1 SAGA, 2 SVRG inner, 3 SVRG refresh (direction = full
 // gradient at the snapshot).
 template <int ALGO>
-__global__ void __launch_bounds__(256) k_update(UpdArgs a) {
+__device__ __forceinline__ void upd_body(const UpdArgs &a, int bx, int by, int z) {
   __shared__ float tin[32][33];
   __shared__ float tout[32][33];
   __shared__ float s_tau;
+  __shared__ int s_sub;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32, z = blockIdx.z;
+  const int x0 = bx * 32, y0 = by * 32;
   const size_t sl = (size_t)z * a.nx * a.ny;
   if (tx == 0 && ty == 0) {
-    s_tau = step_of(a);
-    if (blockIdx.x == 0 && blockIdx.y == 0 && z == 0 && a.tau_log) a.tau_log[a.k] = s_tau;
+    const long long k = a.k_dev ? *a.k_dev : a.k;
+    s_tau = step_of(a, k);
+    s_sub = a.subset_dev ? *a.subset_dev : a.subset;
+    if (bx == 0 && by == 0 && z == 0 && a.tau_log) a.tau_log[k] = s_tau;
   }
   if (ALGO != 3) {
     for (int j = ty; j < 32; j += 8) {
@@ -98,7 +103,7 @@ __global__ void __launch_bounds__(256) k_update(UpdArgs a) {
   __syncthreads();
   const float tau = s_tau;
   const float nf = (float)a.n;
-  float *Ti = a.table ? a.table + (size_t)a.subset * a.N : nullptr;
+  float *Ti = a.table ? a.table + (size_t)s_sub * a.N : nullptr;
   for (int j = ty; j < 32; j += 8) {
     const int xx = x0 + tx, yy = y0 + j;
     float xn = 0.f;
@@ -131,6 +136,64 @@ __global__ void __launch_bounds__(256) k_update(UpdArgs a) {
   for (int j = ty; j < 32; j += 8) {
     const int xx = x0 + j, yy = y0 + tx;
     if (xx < a.nx && yy < a.ny) a.xT[sl + (size_t)xx * a.ny + yy] = tout[j][tx];
+  }
+}
+
+template <int ALGO>
+__global__ void __launch_bounds__(256) k_update(UpdArgs a) {
+  upd_body<ALGO>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Job of this block among consecutive block ranges [begin[j], begin[j+1]).
+__device__ __forceinline__ int batch_job(const int *__restrict__ begin, int njobs) {
+  __shared__ int s_job;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if (tid < 32) {
+    int job = 0;
+    for (int base = 0; base < njobs; base += 32) {
+      const int j = base + tid;
+      const unsigned m = __ballot_sync(0xffffffffu, j < njobs && __ldg(&begin[j]) <= (int)blockIdx.x);
+      job = base + __popc(m) - 1;
+      if (m != 0xffffffffu) break;
+    }
+    if (tid == 0) s_job = job;
+  }
+  __syncthreads();
+  return s_job;
+}
+
+// Batched update: each job's blocks tile its image (32x32 tiles per slice).
+template <int ALGO>
+__global__ void __launch_bounds__(256) k_update_batch(const UpdArgs *__restrict__ jobs, const int *__restrict__ begin,
+                                                      int njobs) {
+  __shared__ UpdArgs sa;
+  const int j = batch_job(begin, njobs);
+  if (threadIdx.x == 0 && threadIdx.y == 0) sa = jobs[j];
+  __syncthreads();
+  const int blk = (int)blockIdx.x - __ldg(&begin[j]);
+  const int tx = (sa.nx + 31) / 32, ty = (sa.ny + 31) / 32;
+  upd_body<ALGO>(sa, blk % tx, (blk / tx) % ty, blk / (tx * ty));
+}
+
+struct ClearJob {
+  float *a, *b;
+  size_t N;
+};
+
+__global__ void __launch_bounds__(256) k_clear_batch(const ClearJob *__restrict__ jobs, const int *__restrict__ begin,
+                                                     int njobs) {
+  const int j = batch_job(begin, njobs);
+  const ClearJob c = jobs[j];
+  const int b0 = __ldg(&begin[j]), nb = __ldg(&begin[j + 1]) - b0;
+  const size_t n4 = c.N / 4;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (size_t i = (size_t)(blockIdx.x - b0) * blockDim.x + threadIdx.x; i < n4; i += (size_t)nb * blockDim.x) {
+    reinterpret_cast<float4 *>(c.a)[i] = z;
+    reinterpret_cast<float4 *>(c.b)[i] = z;
+  }
+  for (size_t i = 4 * n4 + (size_t)(blockIdx.x - b0) * blockDim.x + threadIdx.x; i < c.N; i += (size_t)nb * blockDim.x) {
+    c.a[i] = 0.f;
+    c.b[i] = 0.f;
   }
 }
 
@@ -455,6 +518,8 @@ static UpdArgs upd_args(pet_solver *s, int sub, long long k) {
   a.N = s->N; a.n = s->n; a.subset = sub < 0 ? 0 : sub; a.k = k;
   a.rule = s->o.step_rule; a.tau0 = (float)s->o.tau0; a.eta = (float)s->o.eta;
   a.st = s->st; a.tau_log = s->tau_log;
+  a.subset_dev = nullptr;
+  a.k_dev = nullptr;
   return a;
 }
 
@@ -631,3 +696,284 @@ extern "C" pet_status pet_solver_kernel_time(pet_solver *s, double *total_ms, lo
 }
 
 extern "C" long long pet_launch_count(void) { return launch_count(); }
+
+// ----------------------------------------------------------------- batches
+// Many independent reconstructions (each its own plan and solver) advanced together:
+// every iteration is one launch per phase for all of them (fused subset gradient, RDP
+// gradient, estimator + step, accumulator clear), and iters_per_graph iterations are
+// captured once into a CUDA graph that is replayed after uploading each batch epoch's
+// per-instance subset and iteration indices.
+struct pet_batch {
+  std::vector<pet_solver *> s;
+  int nj = 0, E = 8, K = 2, split = 1, algo = PET_SAGA;
+  GradJob *d_gjobs = nullptr;
+  RdpJob *d_rjobs = nullptr;
+  UpdArgs *d_ujobs = nullptr;
+  ClearJob *d_cjobs = nullptr;
+  int *d_gbegin = nullptr, *d_rbegin = nullptr, *d_ubegin = nullptr, *d_cbegin = nullptr;
+  int gblocks = 0, rblocks = 0, ublocks = 0, cblocks = 0;
+  int *d_sub = nullptr;
+  long long *d_k = nullptr;
+  int *h_sub[2] = {nullptr, nullptr};
+  long long *h_k[2] = {nullptr, nullptr};
+  cudaEvent_t up[2] = {nullptr, nullptr};
+  int buf = 0;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+};
+
+static void batch_free(pet_batch *b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (int i = 0; i < 2; ++i) {
+    if (b->up[i]) cudaEventDestroy(b->up[i]);
+    cudaFreeHost(b->h_sub[i]);
+    cudaFreeHost(b->h_k[i]);
+  }
+  cudaFree(b->d_gjobs); cudaFree(b->d_rjobs); cudaFree(b->d_ujobs); cudaFree(b->d_cjobs);
+  cudaFree(b->d_gbegin); cudaFree(b->d_rbegin); cudaFree(b->d_ubegin); cudaFree(b->d_cbegin);
+  cudaFree(b->d_sub); cudaFree(b->d_k);
+  delete b;
+}
+
+extern "C" void pet_batch_destroy(pet_batch *b) { batch_free(b); }
+
+extern "C" pet_status pet_batch_create(pet_solver *const *solvers, int n, int iters_per_graph, pet_batch **out) {
+  if (!solvers || !out || n < 1 || iters_per_graph < 1) return PET_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    const pet_solver *si = solvers[i];
+    if (!si) return PET_ERR_ARG;
+    if (si->o.algo != solvers[0]->o.algo || si->o.algo == PET_SVRG || si->o.deterministic) return PET_ERR_UNSUPPORTED;
+    if (si->plan->T != 1 || si->o.kappa) return PET_ERR_UNSUPPORTED;
+    for (int j = 0; j < i; ++j)
+      if (solvers[j]->plan == si->plan || solvers[j] == si) return PET_ERR_ARG;  // scratch is per plan
+  }
+  pet_batch *b = new pet_batch();
+  b->s.assign(solvers, solvers + n);
+  b->nj = n;
+  b->E = iters_per_graph;
+  b->algo = solvers[0]->o.algo;
+  const size_t ne = (size_t)b->E * n;
+  bool ok = cudaMalloc(&b->d_gjobs, ne * sizeof(GradJob)) == cudaSuccess &&
+            cudaMalloc(&b->d_rjobs, n * sizeof(RdpJob)) == cudaSuccess &&
+            cudaMalloc(&b->d_ujobs, ne * sizeof(UpdArgs)) == cudaSuccess &&
+            cudaMalloc(&b->d_cjobs, n * sizeof(ClearJob)) == cudaSuccess &&
+            cudaMalloc(&b->d_gbegin, (n + 1) * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&b->d_rbegin, (n + 1) * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&b->d_ubegin, (n + 1) * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&b->d_cbegin, (n + 1) * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&b->d_sub, ne * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&b->d_k, ne * sizeof(long long)) == cudaSuccess;
+  for (int i = 0; i < 2 && ok; ++i)
+    ok = cudaMallocHost(&b->h_sub[i], ne * sizeof(int)) == cudaSuccess &&
+         cudaMallocHost(&b->h_k[i], ne * sizeof(long long)) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->up[i], cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaMemset(b->d_sub, 0, ne * sizeof(int)) == cudaSuccess &&
+       cudaMemset(b->d_k, 0, ne * sizeof(long long)) == cudaSuccess;
+  if (!ok) { batch_free(b); return PET_ERR_NOMEM; }
+  *out = b;
+  return PET_OK;
+}
+
+// Job tables for the current buffers of every instance (rebuilt at each run: the
+// stepsize logs may have been reallocated).
+static pet_status batch_tables(pet_batch *b) {
+  const int n = b->nj, E = b->E;
+  std::vector<GradJob> gj((size_t)E * n);
+  std::vector<UpdArgs> uj((size_t)E * n);
+  std::vector<RdpJob> rj(n);
+  std::vector<ClearJob> cj(n);
+  std::vector<int> gb(n + 1), rb(n + 1), ub(n + 1), cb(n + 1);
+  gb[0] = rb[0] = ub[0] = cb[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    pet_solver *s = b->s[i];
+    pet_plan *p = s->plan;
+    for (int j = 0; j < E; ++j) {
+      GradJob &g = gj[(size_t)j * n + i];
+      g.P = p->dp;
+      g.subset_dev = b->d_sub + (size_t)j * n + i;
+      g.x = s->x;
+      g.xT = p->d_xT;
+      g.g = s->g;
+      g.gT = p->d_gT;
+      UpdArgs a = upd_args(s, 0, 0);
+      a.subset_dev = b->d_sub + (size_t)j * n + i;
+      a.k_dev = b->d_k + (size_t)j * n + i;
+      uj[(size_t)j * n + i] = a;
+    }
+    rj[i].a = prior_args(s, s->o.beta);
+    rj[i].x = s->x;
+    rj[i].grad = s->gS;
+    cj[i].a = s->g;
+    cj[i].b = p->d_gT;
+    cj[i].N = s->N;
+    gb[i + 1] = gb[i] + grad_blocks_shape(p->dp, p->vs_max, b->K, b->split);
+    rb[i + 1] = rb[i] + rdp_blocks(p->g.nx, p->g.ny, p->g.nz);
+    ub[i + 1] = ub[i] + ((p->g.nx + 31) / 32) * ((p->g.ny + 31) / 32) * p->g.nz;
+    cb[i + 1] = cb[i] + (int)std::max<size_t>(1, std::min<size_t>(256, (s->N / 4 + 255) / 256));
+  }
+  b->gblocks = gb[n];
+  b->rblocks = rb[n];
+  b->ublocks = ub[n];
+  b->cblocks = cb[n];
+  if (cudaMemcpy(b->d_gjobs, gj.data(), gj.size() * sizeof(GradJob), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_ujobs, uj.data(), uj.size() * sizeof(UpdArgs), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_rjobs, rj.data(), rj.size() * sizeof(RdpJob), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_cjobs, cj.data(), cj.size() * sizeof(ClearJob), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_gbegin, gb.data(), gb.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_rbegin, rb.data(), rb.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_ubegin, ub.data(), ub.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_cbegin, cb.data(), cb.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+    return PET_ERR_CUDA;
+  return PET_OK;
+}
+
+// One batch iteration j of the captured epoch (all instances).
+static pet_status batch_iteration(pet_batch *b, int j, cudaStream_t st) {
+  const int n = b->nj;
+  SCK(launch_grad_batch(b->d_gjobs + (size_t)j * n, b->d_gbegin, n, b->gblocks, b->K, b->split, st));
+  SCK(launch_rdp_batch(b->d_rjobs, b->d_rbegin, n, b->rblocks, st));
+  note_launch();
+  if (b->algo == PET_SAGA)
+    k_update_batch<1><<<b->ublocks, dim3(32, 8), 0, st>>>(b->d_ujobs + (size_t)j * n, b->d_ubegin, n);
+  else
+    k_update_batch<0><<<b->ublocks, dim3(32, 8), 0, st>>>(b->d_ujobs + (size_t)j * n, b->d_ubegin, n);
+  note_launch();
+  k_clear_batch<<<b->cblocks, 256, 0, st>>>(b->d_cjobs, b->d_cbegin, n);
+  SCK(cudaGetLastError());
+  return PET_OK;
+}
+
+extern "C" pet_status pet_batch_set_grad_shape(pet_batch *b, int planes_per_thread, int parts) {
+  if (!b) return PET_ERR_ARG;
+  if (!(planes_per_thread == 1 || planes_per_thread == 2 || planes_per_thread == 4) ||
+      !(parts == 1 || parts == 2 || parts == 4))
+    return PET_ERR_ARG;
+  b->K = planes_per_thread;
+  b->split = parts;
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  return PET_OK;
+}
+
+static pet_status batch_prepare(pet_batch *b, long long niter, cudaStream_t st) {
+  for (pet_solver *s : b->s) {
+    pet_status e = grow_tau_log(s, s->k + niter);
+    if (e != PET_OK) return e;
+    SCK(to_frames(s->plan, s->x, st));
+    if (!s->initialised) {
+      if (s->o.algo == PET_SAGA) {
+        e = saga_init(s, st);
+        if (e != PET_OK) return e;
+      }
+      s->initialised = true;
+    }
+  }
+  return batch_tables(b);
+}
+
+extern "C" pet_status pet_batch_autotune(pet_batch *b, void *stream, int *planes_per_thread, int *parts) {
+  if (!b) return PET_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  pet_status e = batch_prepare(b, 0, st);
+  if (e != PET_OK) return e;
+  SCK(cudaMemsetAsync(b->d_sub, 0, (size_t)b->E * b->nj * sizeof(int), st));
+  cudaEvent_t e0, e1;
+  SCK(cudaEventCreate(&e0));
+  SCK(cudaEventCreate(&e1));
+  const int ks[3] = {1, 2, 4}, ss[3] = {1, 2, 4};
+  float best = 1e30f;
+  int bk = 2, bs = 1;
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) {
+      b->K = ks[a];
+      b->split = ss[c];
+      e = batch_tables(b);
+      if (e != PET_OK) break;
+      float ms = 0.f;
+      for (int it = 0; it < 5; ++it) {
+        if (it == 2) cudaEventRecord(e0, st);
+        launch_grad_batch(b->d_gjobs, b->d_gbegin, b->nj, b->gblocks, b->K, b->split, st);
+      }
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        e = PET_ERR_CUDA;
+        break;
+      }
+      if (ms < best) { best = ms; bk = ks[a]; bs = ss[c]; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->K = bk;
+  b->split = bs;
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (e != PET_OK) return e;
+  e = batch_tables(b);
+  if (e != PET_OK) return e;
+  note_launch();
+  k_clear_batch<<<b->cblocks, 256, 0, st>>>(b->d_cjobs, b->d_cbegin, b->nj);  // discard the trial gradients
+  SCK(cudaGetLastError());
+  SCK(cudaStreamSynchronize(st));
+  if (planes_per_thread) *planes_per_thread = bk;
+  if (parts) *parts = bs;
+  return PET_OK;
+}
+
+extern "C" pet_status pet_batch_run(pet_batch *b, long long niter, void *stream) {
+  if (!b || niter < 0) return PET_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (pet_solver *s : b->s)
+    if (!s->order.empty() && s->k + niter > (long long)s->order.size()) return PET_ERR_ARG;
+  pet_status e = batch_prepare(b, niter, st);
+  if (e != PET_OK) return e;
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  const int n = b->nj, E = b->E;
+  long long done = 0;
+  while (done < niter) {
+    bool plain = niter - done < E;
+    for (pet_solver *s : b->s)
+      if (epoch_has_pc(s, s->k, E)) plain = true;
+    if (plain) {
+      for (pet_solver *s : b->s) {
+        e = iterate(s, s->k, subset_of(s, s->k), st);
+        if (e != PET_OK) return e;
+        s->k += 1;
+      }
+      done += 1;
+      continue;
+    }
+    if (!b->exec) {
+      cudaGraph_t graph = nullptr;
+      const long long before = launch_count();
+      SCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+      pet_status ie = PET_OK;
+      for (int j = 0; j < E && ie == PET_OK; ++j) ie = batch_iteration(b, j, b->cap);
+      const cudaError_t ce = cudaStreamEndCapture(b->cap, &graph);
+      note_launch(-(launch_count() - before));
+      if (ie != PET_OK) { if (graph) cudaGraphDestroy(graph); return ie; }
+      if (ce != cudaSuccess) return PET_ERR_CUDA;
+      const cudaError_t ie2 = cudaGraphInstantiate(&b->exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie2 != cudaSuccess) return PET_ERR_CUDA;
+    }
+    const int bb = b->buf;
+    b->buf ^= 1;
+    SCK(cudaEventSynchronize(b->up[bb]));  // the previous upload from this host buffer is done
+    for (int j = 0; j < E; ++j)
+      for (int i = 0; i < n; ++i) {
+        pet_solver *s = b->s[i];
+        b->h_sub[bb][(size_t)j * n + i] = subset_of(s, s->k + j);
+        b->h_k[bb][(size_t)j * n + i] = s->k + j;
+      }
+    SCK(cudaMemcpyAsync(b->d_sub, b->h_sub[bb], (size_t)E * n * sizeof(int), cudaMemcpyHostToDevice, st));
+    SCK(cudaMemcpyAsync(b->d_k, b->h_k[bb], (size_t)E * n * sizeof(long long), cudaMemcpyHostToDevice, st));
+    SCK(cudaEventRecord(b->up[bb], st));
+    SCK(cudaGraphLaunch(b->exec, st));
+    note_launch(4LL * E);
+    for (pet_solver *s : b->s) s->k += E;
+    done += E;
+  }
+  return PET_OK;
+}

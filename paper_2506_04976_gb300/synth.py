@@ -16,7 +16,7 @@ below are those of the five benchmark configurations):
   c1  2D 64x64 at 2 mm, 96 radial x 90 views, 1e5 counts, 10% uniform background.
   c2  3D 128x128x47 at 2x2x2.8 mm, 250 radial x 168 views x 109 planes, 1e7 counts.
   c3  c2 with 11 TOF bins (FWHM 390 ps), 1e6 counts.
-  c4  32 instances 96..192 pixels, 1..35 slices (see ``batch_instances``).
+  c4  32 instances 96..192 pixels, 1..35 slices (see ``batch_specs``).
   c5  215x215x71 at 1.3x1.3x2.0 mm, 357 radial x 224 views x 1293 planes x 13 TOF.
 """
 from __future__ import annotations
@@ -345,7 +345,7 @@ def make_problem(name: str = "c1", seed: int = 0, **over):
         nx = over.get("nx", 64)
         geom = dict(nx=nx, ny=nx, nz=1, dx=2.0 * 64 / nx, dy=2.0 * 64 / nx, dz=2.0,
                     nrad=over.get("nrad", 96), nview=over.get("nview", 90),
-                    drad=2.0 * 96 / over.get("nrad", 96), rdet=300.0, ntof=1,
+                    drad=over.get("drad", 2.0 * 96 / over.get("nrad", 96)), rdet=300.0, ntof=1,
                     tof_sigma=1.0, tof_bin=1.0)
         geom["z1"], geom["z2"] = planes_2d()
         geom["ring_z"] = np.zeros(1)
@@ -363,7 +363,7 @@ def make_problem(name: str = "c1", seed: int = 0, **over):
         T = over.get("ntof", 11 if tof else 1)
         geom = dict(nx=nx, ny=nx, nz=nz, dx=dxy, dy=dxy, dz=dz,
                     nrad=over.get("nrad", 250), nview=over.get("nview", 168),
-                    drad=2.0 * 250 / over.get("nrad", 250), rdet=300.0, ntof=T,
+                    drad=over.get("drad", 2.0 * 250 / over.get("nrad", 250)), rdet=300.0, ntof=T,
                     tof_sigma=tof_sigma_mm(390.0),
                     tof_bin=float(math.ceil(math.hypot(nx * dxy, nx * dxy) / T)) if T > 1 else 1.0)
         geom["z1"], geom["z2"] = planes_span3_segments(nrings, pitch)
@@ -432,6 +432,29 @@ def make_problem(name: str = "c1", seed: int = 0, **over):
     return dict(name=name, seed=seed, geom=geom, x_true=s * x_phantom, mu=mu, sens=sens,
                 y=y.astype(ydt), r=r.astype(np.float32), mask=mask.astype(np.uint8),
                 bg=bgmask.astype(np.uint8), **params)
+
+
+def batch_specs(seed: int = 0, count: int = 32):
+    """Per-instance sizes of the batched workload: Nx = Ny uniform in [96, 192] (multiple
+    of 8), Nz odd in [1, 35], R = round(1.95 Nx), n uniform in [8, 28],
+    V = n round(1.31 Nx / n), beta log-uniform in [0.01, 1], counts log-uniform in
+    [1e5, 1e8].  Each entry is a keyword set for make_problem."""
+    u = uniform(seed, 71, 8 * count).reshape(count, 8)
+    out = []
+    for i in range(count):
+        nx = 96 + 8 * int(u[i, 0] * 13)
+        nz = 1 + 2 * int(u[i, 1] * 18)
+        n = 8 + int(u[i, 2] * 21)
+        nview = n * max(1, int(round(1.31 * nx / n)))
+        beta = float(10 ** (-2 + 2 * u[i, 3]))
+        counts = float(10 ** (5 + 3 * u[i, 4]))
+        name = "c1" if nz == 1 else "c2"
+        spec = dict(name=name, nx=nx, nrad=int(round(1.95 * nx)), nview=nview, nsub=n, beta=beta,
+                    counts=counts)
+        if nz > 1:
+            spec["nz"] = nz
+        out.append(spec)
+    return out
 
 
 def random_sinogram_like(geom, seed: int, lo=0.5, hi=1.5):

@@ -1,0 +1,117 @@
+"""Batched instances (uneven sizes, betas, count levels and subset counts) advanced by
+one launch per phase: each instance's result equals the same solver run alone (up to
+the atomics' summation order) and, for one instance, the FP64 oracle's trajectory."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2506_04976_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+SPECS = [
+    dict(name="c1", nx=48, nrad=72, nview=60, nsub=6, beta=0.05, counts=3e5),
+    dict(name="c2", nx=32, nz=9, nrad=64, nview=28, nsub=7, beta=0.5, counts=2e6),
+    dict(name="c1", nx=40, nrad=80, nview=40, nsub=8, beta=0.2, counts=1e6),
+    dict(name="c2", nx=24, nz=5, nrad=48, nview=30, nsub=5, beta=0.01, counts=1e7),
+]
+
+
+def _instances():
+    from paper_2506_04976_gb300 import binding as pet
+    out = []
+    for i, sp in enumerate(SPECS):
+        sp = dict(sp)
+        name = sp.pop("name")
+        p = synth.make_problem(name, 10 + i, **sp)
+        plan = pet.Plan(p["geom"], p["nsub"])
+        mu32, sens32 = p["mu"].astype(np.float32), p["sens"].astype(np.float32)
+        plan.set_data(torch.from_numpy(p["y"].astype(np.int32)).to(DEV), torch.from_numpy(p["r"]).to(DEV),
+                      torch.from_numpy(mu32).to(DEV), torch.from_numpy(sens32).to(DEV))
+        x0 = np.full(plan.img_shape, float(p["x_true"].mean()), np.float32)
+        out.append((p, plan, mu32, sens32, x0))
+    return out
+
+
+def _solver(pet, p, plan, x0, seed, algo):
+    n = p["nsub"]
+    s = pet.Solver(plan, algo=algo, step_rule=pet.STEP_VANISH, tau0=1.0, eta=0.02, precond_kind=1,
+                   pc_iters=(0, n), beta=p["beta"], gamma=p["gamma"], eps=p["eps"], seed=seed)
+    s.set_image(torch.from_numpy(x0).to(DEV))
+    return s
+
+
+@pytest.mark.parametrize("algo", ["saga", "sgd"])
+def test_batch_matches_single_runs_and_oracle(algo):
+    from paper_2506_04976_gb300 import binding as pet
+    A = pet.SAGA if algo == "saga" else pet.SGD
+    inst = _instances()
+    E, niter = 4, 3 * 4 + 19  # graph epochs, plain windows (preconditioner updates) and a tail
+    solvers = [_solver(pet, p, plan, x0, 100 + i, A) for i, (p, plan, _, _, x0) in enumerate(inst)]
+    b = pet.Batch(solvers, iters_per_graph=E)
+    b.run(niter)
+    torch.cuda.synchronize()
+    xb = [s.image().cpu().numpy().astype(np.float64) for s in solvers]
+    taus_b = [s.taus() for s in solvers]
+    del b
+    for i, (p, plan, mu32, sens32, x0) in enumerate(inst):
+        s1 = _solver(pet, p, plan, x0, 100 + i, A)
+        s1.run(niter)
+        torch.cuda.synchronize()
+        x1 = s1.image().cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(xb[i] - x1) <= 1e-5 * np.linalg.norm(x1), i
+        assert np.array_equal(taus_b[i], s1.taus())
+    # instance 1 (3D) against the oracle with the same subset order
+    p, plan, mu32, sens32, x0 = inst[1]
+    G = O.Geometry(p["geom"])
+    m = O.multiplicative(G, mu32, sens32)
+    n = p["nsub"]
+    xo, _, _ = O.solve(G, x0, m, p["r"], p["y"], O.sensitivity(G, 1, -1, m), algo=A, nsub=n, niter=niter,
+                       order=O.subset_order(101, n, niter), step_rule=O.STEP_VANISH, tau0=1.0, eta=0.02,
+                       precond_kind=1, pc_iters=(0, n), beta=p["beta"], gamma=p["gamma"], eps=p["eps"])
+    assert np.linalg.norm(xb[1] - xo) <= 1e-4 * np.linalg.norm(xo)
+
+
+def test_batch_autotune_and_shapes():
+    from paper_2506_04976_gb300 import binding as pet
+    inst = _instances()
+    results = []
+    for shape in ("auto", (1, 1), (4, 4)):
+        solvers = [_solver(pet, p, plan, x0, 200 + i, pet.SAGA) for i, (p, plan, _, _, x0) in enumerate(inst)]
+        b = pet.Batch(solvers, iters_per_graph=5)
+        if shape == "auto":
+            k, sp = b.autotune()
+            assert k in (1, 2, 4) and sp in (1, 2, 4)
+        else:
+            b.set_grad_shape(*shape)
+        b.run(2 * 5 + 8)
+        torch.cuda.synchronize()
+        results.append([s.image().cpu().numpy().astype(np.float64) for s in solvers])
+        del b, solvers
+    for other in results[1:]:
+        for a, c in zip(results[0], other):
+            assert np.linalg.norm(a - c) <= 1e-5 * np.linalg.norm(a)
+
+
+def test_batch_rejects_shared_plans_and_svrg():
+    from paper_2506_04976_gb300 import binding as pet
+    p, plan, _, _, x0 = _instances()[0]
+    s1 = _solver(pet, p, plan, x0, 1, pet.SAGA)
+    s2 = _solver(pet, p, plan, x0, 2, pet.SAGA)
+    with pytest.raises(pet.PetError):
+        pet.Batch([s1, s2])
+    s3 = pet.Solver(plan, algo=pet.SVRG, beta=p["beta"])
+    with pytest.raises(pet.PetError):
+        pet.Batch([s3])
+
+
+def test_c4_specs_shape():
+    sp = synth.batch_specs(0, 32)
+    assert len(sp) == 32
+    for s in sp:
+        assert 96 <= s["nx"] <= 192 and s["nx"] % 8 == 0
+        assert 8 <= s["nsub"] <= 28 and s["nview"] % s["nsub"] == 0
+        assert s["nrad"] == round(1.95 * s["nx"])
+        assert 0.01 <= s["beta"] <= 1 and 1e5 <= s["counts"] <= 1e8
