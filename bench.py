@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-nrmse", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--mode", default="step", choices=["step", "grad"],
+    ap.add_argument("--mode", default="step", choices=["step", "grad", "c4", "c5"],
                     help="grad: only the fused subset-gradient op, for profiler captures")
     ap.add_argument("--shape", default="auto",
                     help="grad mode: 'auto' (autotuner) or 'K,S' planes per thread, parts per LOR")
@@ -249,6 +249,118 @@ def time_to_nrmse(pet, dev, config, seed=0, threshold=0.01, max_epochs=3000):
     return out
 
 
+def run_batched(args, pet, dev, E=8):
+    """32 independent reconstructions of uneven size (c4): SAGA with harmonic
+    preconditioner, advanced by the batched driver (one launch per phase, one graph
+    per window of E iterations) and, for comparison, by the same solvers run one
+    after another.  Units: subset gradients (one per instance per iteration)."""
+    import torch
+    from paper_2506_04976_gb300 import synth
+    t0 = time.perf_counter()
+    plans, solvers, keep = [], [], []
+    for i, sp in enumerate(synth.batch_specs(0, 32)):
+        sp = dict(sp)
+        name = sp.pop("name")
+        p = synth.make_problem(name, 100 + i, **sp)
+        plan = pet.Plan(p["geom"], p["nsub"])
+        y = p["y"].view(np.int16) if p["y"].dtype == np.uint16 else p["y"].astype(np.int32)
+        tensors = [torch.from_numpy(y).to(dev), torch.from_numpy(p["r"]).to(dev),
+                   torch.from_numpy(p["mu"].astype(np.float32)).to(dev),
+                   torch.from_numpy(p["sens"].astype(np.float32)).to(dev)]
+        plan.set_data(*tensors)
+        keep.append(tensors)
+        x0 = torch.full(plan.img_shape, float(p["x_true"].mean()), device=dev)
+        sv = pet.Solver(plan, algo=pet.SAGA, step_rule=pet.STEP_VANISH, tau0=1.0, eta=0.02, precond_kind=1,
+                        pc_iters=(0,), beta=p["beta"], gamma=p["gamma"], eps=p["eps"], seed=500 + i)
+        sv.set_image(x0)
+        plans.append(plan)
+        solvers.append(sv)
+    setup_s = time.perf_counter() - t0
+    batch = pet.Batch(solvers, iters_per_graph=E)
+    shape = batch.autotune()
+    batch.run(E * (1 + args.warmup))  # first window is plain (preconditioner update at k = 0)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = pet.launch_count()
+    a.record()
+    batch.run(E * args.steps)
+    b.record()
+    torch.cuda.synchronize()
+    t_batch = a.elapsed_time(b) / 1e3
+    l_batch = pet.launch_count() - l0
+    del batch
+    for plan in plans:
+        plan.autotune()
+    for sv in solvers:
+        sv.run(E)
+    torch.cuda.synchronize()
+    l0 = pet.launch_count()
+    a.record()
+    for _ in range(args.steps):
+        for sv in solvers:
+            sv.run(E)
+    b.record()
+    torch.cuda.synchronize()
+    t_seq = a.elapsed_time(b) / 1e3
+    l_seq = pet.launch_count() - l0
+    units = 32 * E * args.steps
+    print(json.dumps({"mode": "c4", "workload": "32 SAGA reconstructions, 96..192 px, 1..35 slices, 8..28 subsets",
+                      "units": units, "batched": {"subset_grads_per_s": units / t_batch, "seconds": t_batch,
+                                                  "launches": l_batch, "grad_shape": shape},
+                      "sequential": {"subset_grads_per_s": units / t_seq, "seconds": t_seq, "launches": l_seq},
+                      "setup_s": setup_s}), flush=True)
+
+
+def run_c5(args, pet, dev):
+    """Large TOF workload (215x215x71; 357 x 224 x 1293 x 13 TOF bins): subset gradients
+    (fused TOF forward, KL ratio, backprojection + RDP) on device-generated data, and one
+    SVRG outer loop (74 subset gradients)."""
+    import torch
+    from paper_2506_04976_gb300 import synth
+    t0 = time.perf_counter()
+    p = synth.make_problem_device("c5", 0, device=dev)
+    t1 = time.perf_counter()
+    n = p["nsub"]
+    plan = pet.Plan(p["geom"], n)
+    plan.set_data(p["y"], p["r"], torch.from_numpy(p["mu"].astype(np.float32)).to(dev), p["sens"])
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    shape = plan.autotune()
+    x = torch.from_numpy(np.maximum(p["x_true"], 0.05 * p["x_true"].max()).astype(np.float32)).to(dev)
+    g = torch.empty_like(x)
+    prior = (p["beta"] / n, p["gamma"], p["eps"])
+    for s in range(args.warmup):
+        plan.objective_grad(x, s, prior=prior, g=g, want_obj=False)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for s in range(args.steps):
+        plan.objective_grad(x, s % n, prior=prior, g=g, want_obj=False)
+    b.record()
+    torch.cuda.synchronize()
+    t_grad = a.elapsed_time(b) / 1e3 / args.steps
+    solver = pet.Solver(plan, algo=pet.SVRG, beta=p["beta"], gamma=p["gamma"], eps=p["eps"],
+                        pc_iters=(0,), seed=5)
+    solver.set_image(x)
+    solver.run(2 * n)  # warm-up outer loop (plain: preconditioner update at k = 0)
+    torch.cuda.synchronize()
+    solver.profile(True)
+    a.record()
+    solver.run(2 * n)
+    b.record()
+    torch.cuda.synchronize()
+    t_loop = a.elapsed_time(b) / 1e3
+    kms, kn = solver.kernel_time()
+    lors = 9 * 1293 * 357
+    samples = lors * 215  # about one bilinear sample per driving plane
+    print(json.dumps({"mode": "c5", "generate_s": t1 - t0, "set_data_s": t2 - t1, "grad_shape": shape,
+                      "subset_grad_ms": 1e3 * t_grad, "subset_grads_per_s": 1.0 / t_grad,
+                      "svrg_outer_loop_s": t_loop, "svrg_subset_grads_per_s": (3 * n - 1) / t_loop,
+                      "fused_kernel_ms": kms / max(kn, 1), "fused_launches": kn,
+                      "tof_bin_updates_per_s": lors * 13 / (kms / max(kn, 1) * 1e-3),
+                      "samples_per_s_fwd_and_back": 2 * samples / (kms / max(kn, 1) * 1e-3)}), flush=True)
+
+
 def run_grad_only(args, pet, dev):
     """Subset gradients only (objective_grad on successive subsets), for ncu captures."""
     import torch
@@ -295,6 +407,10 @@ def main():
 
     if args.mode == "grad":
         return run_grad_only(args, pet, dev)
+    if args.mode == "c4":
+        return run_batched(args, pet, dev)
+    if args.mode == "c5":
+        return run_c5(args, pet, dev)
     p = make_inputs(rank)
     g = p["geom"]
     n = p["nsub"]

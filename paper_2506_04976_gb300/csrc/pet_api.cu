@@ -58,6 +58,7 @@ static void plan_free(pet_plan *p) {
   cudaFree(p->d_m); cudaFree(p->d_sens); cudaFree(p->d_sens_sub);
   cudaFree(p->d_xT); cudaFree(p->d_gT); cudaFree(p->d_part); cudaFree(p->d_err);
   cudaFree(p->d_fpart); cudaFree(p->d_fscalar); cudaFree(p->d_qtmp); cudaFree(p->d_img);
+  cudaFree(p->d_groups); cudaFree(p->d_gzd); cudaFree(p->d_gplane); cudaFree(p->d_gzs);
   delete p;
 }
 
@@ -161,6 +162,43 @@ extern "C" pet_status pet_plan_create(const pet_geometry *geom, pet_plan **out) 
   dp.view = pl->d_view; dp.vr = pl->d_vr; dp.plane = pl->d_plane;
   dp.m = pl->d_m; dp.err = pl->d_err;
   pl->dd.view_aff = pl->d_aff;
+  {
+    // plane groups by axial slope, sorted by axial centre (deterministic backprojector)
+    std::vector<int> order(P);
+    for (int p = 0; p < P; ++p) order[p] = p;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      if (plane[a].y != plane[b].y) return plane[a].y < plane[b].y;
+      return plane[a].x < plane[b].x;
+    });
+    std::vector<int2> groups;
+    std::vector<float> gzd, gzs(P);
+    for (int k = 0; k < P; ++k) {
+      gzs[k] = plane[order[k]].x;
+      if (k == 0 || plane[order[k]].y != plane[order[k - 1]].y) {
+        groups.push_back(make_int2(k, 0));
+        gzd.push_back(plane[order[k]].y);
+      }
+      groups.back().y += 1;
+    }
+    const int ng = (int)groups.size();
+    if (dalloc(&pl->d_groups, ng) != cudaSuccess || dalloc(&pl->d_gzd, ng) != cudaSuccess ||
+        dalloc(&pl->d_gplane, P) != cudaSuccess || dalloc(&pl->d_gzs, P) != cudaSuccess) {
+      plan_free(pl);
+      return PET_ERR_NOMEM;
+    }
+    if (cudaMemcpy(pl->d_groups, groups.data(), ng * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(pl->d_gzd, gzd.data(), ng * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(pl->d_gplane, order.data(), P * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(pl->d_gzs, gzs.data(), P * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+      plan_free(pl);
+      return PET_ERR_CUDA;
+    }
+    pl->dd.ngroups = ng;
+    pl->dd.groups = pl->d_groups;
+    pl->dd.gzd = pl->d_gzd;
+    pl->dd.gplane = pl->d_gplane;
+    pl->dd.gzs = pl->d_gzs;
+  }
   *out = pl;
   return PET_OK;
 }

@@ -46,8 +46,16 @@ struct DevPlan {
 
 // Per-view data for the voxel-driven (deterministic) backprojector: fb0 is affine in
 // the radial index, fb0(v, r) ~ fbA + r fbB, used only to find candidate LORs.
+// Planes are grouped by their axial slope zd (equal FP32 values); within a group they
+// are listed by increasing zs, so the planes whose ray can reach a given slice are a
+// contiguous run found by binary search.
 struct DevPlanDet {
   const float2 *view_aff;  // [V] {fbA, fbB}
+  int ngroups;
+  const int2 *groups;      // [ngroups] {first index into gplane, count}
+  const float *gzd;        // [ngroups] zd of the group
+  const int *gplane;       // [P] plane indices, grouped, sorted by zs within a group
+  const float *gzs;        // [P] zs of gplane[k]
 };
 
 struct Lor {

@@ -18,6 +18,9 @@ struct pet_plan {
   // geometry tables
   float4 *d_view = nullptr, *d_vr = nullptr, *d_plane = nullptr;
   float2 *d_aff = nullptr;
+  int2 *d_groups = nullptr;    // deterministic backprojector: plane groups
+  float *d_gzd = nullptr, *d_gzs = nullptr;
+  int *d_gplane = nullptr;
   // derived data
   float *d_m = nullptr;         // [V][P][R] multiplicative factors
   float *d_sens = nullptr;      // [N] A^T 1

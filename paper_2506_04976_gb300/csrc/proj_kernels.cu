@@ -590,7 +590,20 @@ __global__ void __launch_bounds__(kBlock) k_back_det(DevPlan P, DevPlanDet D, in
       else continue;
       const float t0b = vr.y, inv2h = vr.z;
       const float g1 = dau * inv2h, g2 = t0b * inv2h;
-      for (int p = 0; p < P.nplane; ++p) {
+      const float cz = fmaf((float)i, g1, g2);  // fz ~ zs + zd * cz
+      for (int gi = 0; gi < D.ngroups; ++gi) {
+        const int2 gr = __ldg(&D.groups[gi]);
+        const float zd = __ldg(&D.gzd[gi]);
+        const float lo_zs = (float)(iz - 1) - zd * cz - 1e-3f;
+        const float hi_zs = (float)(iz + 1) - zd * cz + 1e-3f;
+        int a = gr.x, b = gr.x + gr.y;  // first zs >= lo_zs
+        while (a < b) {
+          const int mid = (a + b) >> 1;
+          if (__ldg(&D.gzs[mid]) < lo_zs) a = mid + 1;
+          else b = mid;
+        }
+        for (int kq = a; kq < gr.x + gr.y && __ldg(&D.gzs[kq]) <= hi_zs; ++kq) {
+        const int p = __ldg(&D.gplane[kq]);
         const float4 pl = __ldg(&P.plane[p]);
         const float dfz = g1 * pl.y;
         const float fz0 = fmaf(g2, pl.y, pl.x);
@@ -627,6 +640,7 @@ __global__ void __launch_bounds__(kBlock) k_back_det(DevPlan P, DevPlanDet D, in
           }
         }
         kahan_add(sum, cmp, mL * val * (wbj * wzk));
+        }
       }
     }
   }

@@ -334,13 +334,8 @@ def _smooth(a, sigma):
     return gaussian_filter(a, sigma, mode="nearest")
 
 
-def make_problem(name: str = "c1", seed: int = 0, **over):
-    """Returns a dict describing one reconstruction problem (geometry, phantom, data).
-
-    Keys: geom (for both the CUDA plan and the oracle), x_true (nz,ny,nx), mu
-    (nz,ny,nx), sens (V,P,R), y (V,P,R,T) integer counts, r (V,P,R,T), mask and bg
-    (NRMSE masks), and the reconstruction parameters nsub, beta, gamma, eps.
-    Overrides shrink a workload (nx, nz, nrad, nview, nrings, ...) for quick tests."""
+def _setup(name: str, seed: int, **over):
+    """Geometry, phantom and reconstruction parameters of a workload (no data)."""
     if name == "c1":
         nx = over.get("nx", 64)
         geom = dict(nx=nx, ny=nx, nz=1, dx=2.0 * 64 / nx, dy=2.0 * 64 / nx, dz=2.0,
@@ -397,6 +392,30 @@ def make_problem(name: str = "c1", seed: int = 0, **over):
     spacing = (geom["dx"], geom["dy"], geom["dz"])
     x_phantom = voxelise(ells, shape, spacing)
     mu = voxelise(mu_ells, shape, spacing)
+    from scipy.ndimage import binary_dilation
+    mask = binary_dilation(x_phantom > 0, np.ones((3, 3, 3) if geom["nz"] > 1 else (1, 3, 3), bool))
+    bgmask = (x_phantom == bgval)
+    if params["beta"] is None:
+        # beta scaled with the count level as in Sec. 3.1 (relative strength 4)
+        params["beta"] = 4.0 * 2e-4 * counts / 3e7
+    return dict(name=name, seed=seed, geom=geom, mu=mu, mask=mask.astype(np.uint8),
+                bg=bgmask.astype(np.uint8), _ells=ells, _mu_ells=mu_ells, _x_phantom=x_phantom,
+                _counts=counts, _frac=frac, _smooth=smooth, **params)
+
+
+def make_problem(name: str = "c1", seed: int = 0, **over):
+    """Returns a dict describing one reconstruction problem (geometry, phantom, data).
+
+    Keys: geom (for both the CUDA plan and the oracle), x_true (nz,ny,nx), mu
+    (nz,ny,nx), sens (V,P,R), y (V,P,R,T) integer counts, r (V,P,R,T), mask and bg
+    (NRMSE masks), and the reconstruction parameters nsub, beta, gamma, eps.
+    Overrides shrink a workload (nx, nz, nrad, nview, nrings, ...) for quick tests."""
+    base = _setup(name, seed, **over)
+    geom = base["geom"]
+    ells, mu_ells = base["_ells"], base["_mu_ells"]
+    x_phantom = base["_x_phantom"]
+    counts, frac, smooth = base["_counts"], base["_frac"], base["_smooth"]
+
     sens = crystal_sensitivity(geom, seed) if geom["nz"] > 1 or name != "c1" else np.ones(
         (geom["nview"], len(geom["z1"]), geom["nrad"]))
     T = geom["ntof"] if geom["ntof"] > 1 else 1
@@ -423,15 +442,9 @@ def make_problem(name: str = "c1", seed: int = 0, **over):
     lam_s = s * lam
     y = poisson(lam_s + r, seed, 41).reshape(lam.shape)
     ydt = np.uint16 if y.max() < 65536 else np.uint32
-    from scipy.ndimage import binary_dilation
-    mask = binary_dilation(x_phantom > 0, np.ones((3, 3, 3) if geom["nz"] > 1 else (1, 3, 3), bool))
-    bgmask = (x_phantom == bgval)
-    if params["beta"] is None:
-        # beta scaled with the count level as in Sec. 3.1 (relative strength 4)
-        params["beta"] = 4.0 * 2e-4 * counts / 3e7
-    return dict(name=name, seed=seed, geom=geom, x_true=s * x_phantom, mu=mu, sens=sens,
-                y=y.astype(ydt), r=r.astype(np.float32), mask=mask.astype(np.uint8),
-                bg=bgmask.astype(np.uint8), **params)
+    out = {k: v for k, v in base.items() if not k.startswith("_")}
+    out.update(x_true=s * x_phantom, sens=sens, y=y.astype(ydt), r=r.astype(np.float32))
+    return out
 
 
 def batch_specs(seed: int = 0, count: int = 32):
@@ -467,3 +480,131 @@ def random_sinogram_like(geom, seed: int, lo=0.5, hi=1.5):
 def random_image_like(geom, seed: int, lo=0.0, hi=1.0):
     shape = (geom["nz"], geom["ny"], geom["nx"])
     return lo + (hi - lo) * uniform(seed, 61, int(np.prod(shape))).reshape(shape)
+
+
+# ------------------------------------------------------------- device generator
+def make_problem_device(name: str = "c5", seed: int = 0, device="cuda", views_per_chunk: int = 8, **over):
+    """As make_problem, but builds the expected counts, background and Poisson counts
+    with torch on `device` (for workloads too large for the host generator, e.g. c5:
+    1.34 G TOF bins).  Same phantom, scanner and physics (exact ellipsoid chords, the
+    closed-form untruncated-Gaussian TOF integral, crystal efficiencies, smooth
+    background); counts come from torch's seeded Poisson sampler, so they differ from
+    the host generator's draws.  Returns torch tensors for y (int16 holding uint16 or
+    int32), r (float32), sens (float32) and numpy arrays for the image-domain fields."""
+    import torch
+    base = _setup(name, seed, **over)
+    geom = base["geom"]
+    V, P, R = geom["nview"], len(geom["z1"]), geom["nrad"]
+    T = geom["ntof"] if geom["ntof"] > 1 else 1
+    dev = torch.device(device)
+    f64 = torch.float64
+    ells, mu_ells = base["_ells"], base["_mu_ells"]
+    z1 = torch.tensor(np.asarray(geom["z1"]), dtype=f64, device=dev)
+    z2 = torch.tensor(np.asarray(geom["z2"]), dtype=f64, device=dev)
+    s_r = (torch.arange(R, dtype=f64, device=dev) - 0.5 * (R - 1)) * geom["drad"]
+    h = torch.sqrt(geom["rdet"] ** 2 - s_r ** 2)
+    ring_z = torch.tensor(np.asarray(geom["ring_z"]), dtype=f64, device=dev)
+    nc = 2 * V
+    eff = np.clip(1.0 + 0.05 * normal(seed, 31, nc * len(geom["ring_z"])), 0.8, 1.2).reshape(-1, nc)
+    eff = torch.tensor(eff, dtype=f64, device=dev)
+    lam = torch.empty((V, P, R, T), dtype=torch.float32, device=dev)
+    att = torch.empty((V, P, R), dtype=torch.float32, device=dev)
+    sens = torch.empty((V, P, R), dtype=torch.float32, device=dev)
+    if T > 1:
+        edges = (torch.arange(T + 1, dtype=f64, device=dev) - 0.5 * T) * geom["tof_bin"]
+        sig = geom["tof_sigma"]
+    inv_sqrt2pi = 1.0 / math.sqrt(2.0 * math.pi)
+
+    def Psi(u):
+        return u * 0.5 * torch.erfc(-u / math.sqrt(2.0)) + torch.exp(-0.5 * u * u) * inv_sqrt2pi
+
+    for v0 in range(0, V, views_per_chunk):
+        vs = torch.arange(v0, min(V, v0 + views_per_chunk), dtype=f64, device=dev)
+        phi = vs * math.pi / V
+        c, sn = torch.cos(phi)[:, None, None], torch.sin(phi)[:, None, None]
+        mx, my = s_r[None, None, :] * c, s_r[None, None, :] * sn
+        ux, uy = -sn, c
+        hh = h[None, None, :]
+        e1 = torch.stack([(mx - hh * ux).expand(-1, P, -1), (my - hh * uy).expand(-1, P, -1),
+                          z1[None, :, None].expand(len(vs), -1, R)], -1)
+        e2 = torch.stack([(mx + hh * ux).expand(-1, P, -1), (my + hh * uy).expand(-1, P, -1),
+                          z2[None, :, None].expand(len(vs), -1, R)], -1)
+        d = e2 - e1
+        L = torch.sqrt((d * d).sum(-1))
+
+        def chords(ell):
+            cx, cy, cz, ax, ay, az, th, _ = ell
+            ct, st = math.cos(th), math.sin(th)
+            px, py, pz = e1[..., 0] - cx, e1[..., 1] - cy, e1[..., 2] - cz
+            qx = (px * ct + py * st) / ax
+            qy = (-px * st + py * ct) / ay
+            qz = pz / az
+            vx = (d[..., 0] * ct + d[..., 1] * st) / ax
+            vy = (-d[..., 0] * st + d[..., 1] * ct) / ay
+            vz = d[..., 2] / az
+            A = vx * vx + vy * vy + vz * vz
+            B = 2.0 * (qx * vx + qy * vy + qz * vz)
+            Cc = qx * qx + qy * qy + qz * qz - 1.0
+            disc = B * B - 4.0 * A * Cc
+            ok = disc > 0
+            sq = torch.sqrt(torch.clamp(disc, min=0.0))
+            l1 = torch.where(ok, (-B - sq) / (2.0 * A), torch.zeros_like(A)).clamp(0.0, 1.0)
+            l2 = torch.where(ok, (-B + sq) / (2.0 * A), torch.zeros_like(A)).clamp(0.0, 1.0)
+            return l1, l2
+
+        mu_int = torch.zeros_like(L)
+        for ell in mu_ells:
+            l1, l2 = chords(ell)
+            mu_int += ell[7] * (l2 - l1).clamp(min=0.0) * L
+        acc = torch.zeros(L.shape + (T,), dtype=f64, device=dev)
+        for ell in ells:
+            l1, l2 = chords(ell)
+            seg = l2 > l1
+            if T == 1:
+                acc[..., 0] += torch.where(seg, ell[7] * (l2 - l1) * L, torch.zeros_like(L))
+            else:
+                t1 = ((l1 - 0.5) * L)[..., None]
+                t2 = ((l2 - 0.5) * L)[..., None]
+                F = sig * (Psi((edges - t1) / sig) - Psi((edges - t2) / sig))
+                acc += torch.where(seg[..., None], ell[7] * (F[..., 1:] - F[..., :-1]), torch.zeros_like(acc))
+
+        def crystal(ex, ey, ez):
+            ang = torch.remainder(torch.atan2(ey, ex), 2 * math.pi)
+            ci = torch.remainder(torch.round(ang / (2 * math.pi) * nc).long(), nc)
+            ri = (ez[..., None] - ring_z).abs().argmin(-1)
+            return eff[ri, ci]
+
+        sl = slice(v0, v0 + len(vs))
+        se = crystal(e1[..., 0], e1[..., 1], e1[..., 2]) * crystal(e2[..., 0], e2[..., 1], e2[..., 2])
+        a = torch.exp(-mu_int)
+        sens[sl] = se.float()
+        att[sl] = a.float()
+        lam[sl] = (acc * (se * a)[..., None]).float()
+    counts = base["_counts"]
+    frac = base["_frac"]
+    lam_sum = float(lam.double().sum())
+    s_scale = (1.0 - frac) * counts / lam_sum
+    lam *= s_scale
+    # smooth background: Gaussian-smoothed noise-free data (planes sigma 2, radial sigma 20)
+    bg = lam.sum(-1)
+    for dim, sg in ((1, 2.0), (2, 20.0)):
+        rad = int(4 * sg)
+        k = torch.exp(-0.5 * (torch.arange(-rad, rad + 1, device=dev, dtype=torch.float32) / sg) ** 2)
+        k = (k / k.sum()).view(1, 1, -1)
+        x = bg.movedim(dim, -1)
+        shp = x.shape
+        xp = torch.nn.functional.pad(x.reshape(-1, 1, shp[-1]), (rad, rad), mode="replicate")
+        x = torch.nn.functional.conv1d(xp, k).reshape(shp)
+        bg = x.movedim(-1, dim)
+    r = (frac * counts / float(bg.double().sum())) * (bg[..., None] / T)
+    r = r.expand(-1, -1, -1, T).contiguous()
+    g = torch.Generator(device=dev).manual_seed(seed)
+    y = torch.poisson(lam + r, generator=g)
+    del lam
+    ymax = float(y.max())
+    y = y.to(torch.int32)
+    if ymax < 65536:  # uint16 counts carried in an int16 tensor (same bit pattern)
+        y = (y - 65536 * (y >= 32768).to(torch.int32)).to(torch.int16)
+    out = {k: v for k, v in base.items() if not k.startswith("_")}
+    out.update(y=y, r=r, sens=sens, x_true=s_scale * base["_x_phantom"], counts=counts)
+    return out
