@@ -59,6 +59,7 @@ static void plan_free(pet_plan *p) {
   cudaFree(p->d_xT); cudaFree(p->d_gT); cudaFree(p->d_part); cudaFree(p->d_err);
   cudaFree(p->d_fpart); cudaFree(p->d_fscalar); cudaFree(p->d_qtmp); cudaFree(p->d_img);
   cudaFree(p->d_groups); cudaFree(p->d_gzd); cudaFree(p->d_gplane); cudaFree(p->d_gzs);
+  cudaFree(p->d_erfc_tab);
   delete p;
 }
 
@@ -136,6 +137,7 @@ extern "C" pet_status pet_plan_create(const pet_geometry *geom, pet_plan **out) 
     dp.tof_amax = (float)amax;
     dp.tof_erfc_amax = (float)erfc(amax);
     dp.tof_half_norm = (float)(1.0 / (2.0 * erf(amax)));
+    dp.erfc_scale = (float)(kErfcTab / amax);
   }
   // any fused-gradient launch (up to 4 parts per LOR) has at most this many blocks
   const int gb_all = (int)((4 * nlor + kBlock - 1) / kBlock) + 1;
@@ -162,6 +164,18 @@ extern "C" pet_status pet_plan_create(const pet_geometry *geom, pet_plan **out) 
   dp.view = pl->d_view; dp.vr = pl->d_vr; dp.plane = pl->d_plane;
   dp.m = pl->d_m; dp.err = pl->d_err;
   pl->dd.view_aff = pl->d_aff;
+  if (pl->T > 1) {
+    const double amax = 3.0 / sqrt(2.0);
+    std::vector<float> tab(kErfcTab + 1);
+    for (int j = 0; j <= kErfcTab; ++j) tab[j] = (float)erfc(amax * j / kErfcTab);
+    if (dalloc(&pl->d_erfc_tab, kErfcTab + 1) != cudaSuccess) { plan_free(pl); return PET_ERR_NOMEM; }
+    if (cudaMemcpy(pl->d_erfc_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+      plan_free(pl);
+      return PET_ERR_CUDA;
+    }
+    dp.erfc_tab = pl->d_erfc_tab;
+    dp.tof_erfc_amax = tab[kErfcTab];
+  }
   {
     // plane groups by axial slope, sorted by axial centre (deterministic backprojector)
     std::vector<int> order(P);

@@ -21,6 +21,7 @@ struct pet_plan {
   int2 *d_groups = nullptr;    // deterministic backprojector: plane groups
   float *d_gzd = nullptr, *d_gzs = nullptr;
   int *d_gplane = nullptr;
+  float *d_erfc_tab = nullptr;  // TOF: erfc table
   // derived data
   float *d_m = nullptr;         // [V][P][R] multiplicative factors
   float *d_sens = nullptr;      // [N] A^T 1

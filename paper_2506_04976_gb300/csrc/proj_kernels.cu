@@ -50,7 +50,7 @@ __device__ __forceinline__ int tof_bins(const DevPlan &P) {
 template <int TT, int STRIDE = 1>
 __device__ __forceinline__ void forward_lor(const DevPlan &P, const Lor &L,
                                             const float *__restrict__ img, float (&acc)[TT],
-                                            bool act = true, int off = 0) {
+                                            bool act = true, int off = 0, const float *tab = nullptr) {
   const int Na = L.xdrive ? P.nx : P.ny;
   const int Nb = L.xdrive ? P.ny : P.nx;
   const int plane = Na * Nb;
@@ -69,12 +69,12 @@ __device__ __forceinline__ void forward_lor(const DevPlan &P, const Lor &L,
     } else {
       const float t = fmaf((float)i, L.dt, L.t0);
       const float u0 = (P.tof_e0 - t) * P.tof_inv;
-      float uprev = u0, Gprev = tof_edge_G(P, u0);
+      float uprev = u0, Gprev = tof_edge_G(P, tab, u0);
 #pragma unroll
       for (int k = 1; k <= TT; ++k) {
         if (k <= T) {
           const float u = fmaf((float)k, du, u0);
-          const float G = tof_edge_G(P, u);
+          const float G = tof_edge_G(P, tab, u);
           const float w = tof_bin_weight(P, uprev, Gprev, u, G);
           kahan_add(acc[k - 1], cmp[k - 1], val * w);
           uprev = u;
@@ -88,7 +88,8 @@ __device__ __forceinline__ void forward_lor(const DevPlan &P, const Lor &L,
 // Back: scatter sum_b q[b] w_b(t) * bilinear weights; q already includes m and L.
 template <int TT, int STRIDE = 1>
 __device__ __forceinline__ void back_lor(const DevPlan &P, const Lor &L, float *__restrict__ img,
-                                         const float (&q)[TT], bool act = true, int off = 0) {
+                                         const float (&q)[TT], bool act = true, int off = 0,
+                                         const float *tab = nullptr) {
   const int Na = L.xdrive ? P.nx : P.ny;
   const int Nb = L.xdrive ? P.ny : P.nx;
   const int plane = Na * Nb;
@@ -104,13 +105,13 @@ __device__ __forceinline__ void back_lor(const DevPlan &P, const Lor &L, float *
     } else {
       const float t = fmaf((float)i, L.dt, L.t0);
       const float u0 = (P.tof_e0 - t) * P.tof_inv;
-      float uprev = u0, Gprev = tof_edge_G(P, u0);
+      float uprev = u0, Gprev = tof_edge_G(P, tab, u0);
       val = 0.f;
 #pragma unroll
       for (int k = 1; k <= TT; ++k) {
         if (k <= T) {
           const float u = fmaf((float)k, du, u0);
-          const float G = tof_edge_G(P, u);
+          const float G = tof_edge_G(P, tab, u);
           val = fmaf(q[k - 1], tof_bin_weight(P, uprev, Gprev, u, G), val);
           uprev = u;
           Gprev = G;
@@ -147,12 +148,14 @@ __device__ __forceinline__ LorIdx lor_index(const DevPlan &P, int subset, long l
 template <int TT>
 __global__ void __launch_bounds__(kBlock) k_forward(DevPlan P, int subset, const float *__restrict__ x,
                                                     const float *__restrict__ xT, float *__restrict__ out) {
+  __shared__ float s_tab[TT > 1 ? kErfcTab + 1 : 1];
+  if (TT > 1) load_erfc_tab(P, s_tab);
   const LorIdx id = lor_index(P, subset, (long long)blockIdx.x * blockDim.x + threadIdx.x);
   Lor L = {};
   if (id.ok) lor_setup(P, id.v, id.p, id.r, L);
   warp_uniform_range(L, id.ok);
   float acc[TT];
-  forward_lor<TT>(P, L, L.xdrive ? xT : x, acc, id.ok);
+  forward_lor<TT>(P, L, L.xdrive ? xT : x, acc, id.ok, 0, s_tab);
   if (!id.ok) return;
   const int T = tof_bins<TT>(P);
   const float m = __ldg(&P.m[((size_t)id.v * P.nplane + id.p) * P.nrad + id.r]) * L.L;
@@ -164,6 +167,8 @@ __global__ void __launch_bounds__(kBlock) k_forward(DevPlan P, int subset, const
 template <int TT>
 __global__ void __launch_bounds__(kBlock) k_back(DevPlan P, int subset, const float *__restrict__ q,
                                                  float *__restrict__ g, float *__restrict__ gT) {
+  __shared__ float s_tab[TT > 1 ? kErfcTab + 1 : 1];
+  if (TT > 1) load_erfc_tab(P, s_tab);
   const LorIdx id = lor_index(P, subset, (long long)blockIdx.x * blockDim.x + threadIdx.x);
   Lor L = {};
   if (id.ok) lor_setup(P, id.v, id.p, id.r, L);
@@ -179,7 +184,7 @@ __global__ void __launch_bounds__(kBlock) k_back(DevPlan P, int subset, const fl
       any |= qq[b] != 0.f;
     }
   }
-  back_lor<TT>(P, L, L.xdrive ? gT : g, qq, any);
+  back_lor<TT>(P, L, L.xdrive ? gT : g, qq, any, 0, s_tab);
 }
 
 __device__ __forceinline__ void block_sum_store(double v, double *out) {
@@ -211,6 +216,8 @@ __global__ void __launch_bounds__(kBlock) k_grad(DevPlan P, int subset, const in
                                                  double *__restrict__ kl_part, int mode) {
   constexpr int LPB = kBlock / SPLIT;  // LORs per block
   __shared__ float xs[SPLIT > 1 ? SPLIT : 1][SPLIT > 1 ? LPB : 1][TT];
+  __shared__ float s_tab[TT > 1 ? kErfcTab + 1 : 1];
+  if (TT > 1) load_erfc_tab(P, s_tab);
   if (subset_dev) subset = *subset_dev;
   const int part = threadIdx.x / LPB;
   const int tl = threadIdx.x % LPB;
@@ -221,7 +228,7 @@ __global__ void __launch_bounds__(kBlock) k_grad(DevPlan P, int subset, const in
   warp_uniform_range(L, id.ok);
   float acc[TT];
   if (mode != MODE_SENS) {
-    forward_lor<TT, SPLIT>(P, L, L.xdrive ? xT : x, acc, id.ok, part);
+    forward_lor<TT, SPLIT>(P, L, L.xdrive ? xT : x, acc, id.ok, part, s_tab);
     if (SPLIT > 1) {
 #pragma unroll
       for (int b = 0; b < TT; ++b) xs[part][tl][b] = acc[b];
@@ -269,7 +276,7 @@ __global__ void __launch_bounds__(kBlock) k_grad(DevPlan P, int subset, const in
       }
     }
   }
-  if (mode != MODE_OBJ) back_lor<TT, SPLIT>(P, L, L.xdrive ? gT : g, q, any, part);
+  if (mode != MODE_OBJ) back_lor<TT, SPLIT>(P, L, L.xdrive ? gT : g, q, any, part, s_tab);
   if (kl_part) block_sum_store(kl, kl_part + blockIdx.x);
 }
 
@@ -558,6 +565,9 @@ template <int TT>
 __global__ void __launch_bounds__(kBlock) k_back_det(DevPlan P, DevPlanDet D, int subset,
                                                      const float *__restrict__ q, float *__restrict__ g,
                                                      int ones) {
+  __shared__ float s_tab[TT > 1 ? kErfcTab + 1 : 1];
+  if (TT > 1) load_erfc_tab(P, s_tab);
+  const float *tab = s_tab;
   const int nvox = P.nx * P.ny * P.nz;
   const int vox = blockIdx.x * blockDim.x + threadIdx.x;
   if (vox >= nvox) return;
@@ -625,13 +635,13 @@ __global__ void __launch_bounds__(kBlock) k_back_det(DevPlan P, DevPlanDet D, in
         } else {
           const float t = fmaf((float)i, dau * sec, t0b * sec);
           const float u0 = (P.tof_e0 - t) * P.tof_inv;
-          float uprev = u0, Gprev = tof_edge_G(P, u0);
+          float uprev = u0, Gprev = tof_edge_G(P, tab, u0);
           val = 0.f;
 #pragma unroll
           for (int k = 1; k <= TT; ++k) {
             if (k <= T) {
               const float u = fmaf((float)k, du, u0);
-              const float G = tof_edge_G(P, u);
+              const float G = tof_edge_G(P, tab, u);
               const float qb = ones ? 1.f : __ldg(&q[ql + k - 1]);
               val = fmaf(qb, tof_bin_weight(P, uprev, Gprev, u, G), val);
               uprev = u;
