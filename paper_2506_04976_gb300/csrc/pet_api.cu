@@ -138,6 +138,9 @@ extern "C" pet_status pet_plan_create(const pet_geometry *geom, pet_plan **out) 
     dp.tof_erfc_amax = (float)erfc(amax);
     dp.tof_half_norm = (float)(1.0 / (2.0 * erf(amax)));
     dp.erfc_scale = (float)(kErfcTab / amax);
+    dp.tof_inv_w = (float)(1.0 / g.tof_bin);
+    dp.tof_reach = (float)(3.0 * g.tof_sigma / g.tof_bin);
+    dp.tof_wmax = (int)ceil(6.0 * g.tof_sigma / g.tof_bin) + 3;
   }
   // any fused-gradient launch (up to 4 parts per LOR) has at most this many blocks
   const int gb_all = (int)((4 * nlor + kBlock - 1) / kBlock) + 1;
