@@ -8,7 +8,7 @@
 
 namespace petgb {
 
-constexpr int RDP_TX = 32, RDP_TY = 8, RDP_ZCH = 4;
+constexpr int RDP_TX = 32, RDP_TY = 8, RDP_ZCH = 4;  // tile: 32 x 8 voxels x 4 slices
 
 RdpArgs make_rdp_args(const pet_rdp_params &p) {
   RdpArgs a;
@@ -45,20 +45,18 @@ __device__ __forceinline__ double block_sum_d(double v) {
   return s;  // valid in thread 0
 }
 
-// Per-voxel RDP sums over the 26 neighbours held in the shared-memory planes.  BOUND
-// enables the image-boundary checks (interior tiles skip them).
+// Per-voxel RDP sums over the 26 neighbours held in the shared-memory planes (plane
+// index lz = local z + 1).  BOUND enables the image-boundary checks.
 template <bool KAPPA, bool WG, bool WH, bool VAL, bool BOUND>
 __device__ __forceinline__ void rdp_voxel(const RdpArgs &a, const float (*sx)[RDP_TY + 2][RDP_TX + 2],
-                                          const float (*sk)[RDP_TY + 2][RDP_TX + 2], int z, int gx, int gy,
-                                          int tx, int ty, float &gsum, float &hsum, float &vs) {
-  const int sc = (z + 3) % 3;
-  const float xi = sx[sc][ty + 1][tx + 1];
-  const float ki = KAPPA ? sk[sc][ty + 1][tx + 1] : 1.f;
+                                          const float (*sk)[RDP_TY + 2][RDP_TX + 2], int z, int lz, int gx,
+                                          int gy, int tx, int ty, float &gsum, float &hsum, float &vs) {
+  const float xi = sx[lz][ty + 1][tx + 1];
+  const float ki = KAPPA ? sk[lz][ty + 1][tx + 1] : 1.f;
 #pragma unroll
   for (int oz = -1; oz <= 1; ++oz) {
-    const int jz = z + oz;
-    if (BOUND && (jz < 0 || jz >= a.nz)) continue;
-    const int sl = (jz + 3) % 3;
+    if (BOUND && (z + oz < 0 || z + oz >= a.nz)) continue;
+    const int sl = lz + oz;
 #pragma unroll
     for (int oy = -1; oy <= 1; ++oy) {
       if (BOUND && (gy + oy < 0 || gy + oy >= a.ny)) continue;
@@ -87,56 +85,52 @@ __device__ __forceinline__ void rdp_voxel(const RdpArgs &a, const float (*sx)[RD
   }
 }
 
+// One block: a 32x8 tile over RDP_ZCH slices.  All RDP_ZCH + 2 planes (with halo) are
+// staged in shared memory at once, then every slice is computed without further
+// barriers.
 template <bool KAPPA, bool WG, bool WH, bool VAL>
 __device__ __forceinline__ void rdp_body(const RdpArgs &a, const float *__restrict__ x, float *__restrict__ grad,
                                          float *__restrict__ hdiag, double *__restrict__ val_out, int accumulate,
                                          int blk) {
-  __shared__ float sx[3][RDP_TY + 2][RDP_TX + 2];
-  __shared__ float sk[KAPPA ? 3 : 1][RDP_TY + 2][RDP_TX + 2];
+  __shared__ float sx[RDP_ZCH + 2][RDP_TY + 2][RDP_TX + 2];
+  __shared__ float sk[KAPPA ? RDP_ZCH + 2 : 1][RDP_TY + 2][RDP_TX + 2];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * RDP_TX + tx;
   const int nbx = (a.nx + RDP_TX - 1) / RDP_TX, nby = (a.ny + RDP_TY - 1) / RDP_TY;
   const int bx = blk % nbx, by = (blk / nbx) % nby, bz = blk / (nbx * nby);
   const int x0 = bx * RDP_TX, y0 = by * RDP_TY;
   const int z0 = bz * RDP_ZCH, z1 = min(a.nz, z0 + RDP_ZCH);
   const int nxy = a.nx * a.ny;
-  // the tile and its in-plane halo lie inside the image
   const bool inner_xy = x0 >= 1 && x0 + RDP_TX < a.nx && y0 >= 1 && y0 + RDP_TY < a.ny;
-
-  auto load_plane = [&](int z) {
-    const int slot = (z + 3) % 3;
-    for (int e = tid; e < (RDP_TY + 2) * (RDP_TX + 2); e += RDP_TX * RDP_TY) {
-      const int ly = e / (RDP_TX + 2), lx = e % (RDP_TX + 2);
-      const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-      float v = 0.f, kv = 0.f;
-      if (z >= 0 && z < a.nz && gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny) {
-        const size_t gi = (size_t)z * nxy + (size_t)gy * a.nx + gx;
-        v = __ldg(x + gi);
-        if (KAPPA) kv = __ldg(a.kappa + gi);
-      }
-      sx[slot][ly][lx] = v;
-      if (KAPPA) sk[slot][ly][lx] = kv;
+  constexpr int PLANE = (RDP_TY + 2) * (RDP_TX + 2);
+  for (int e = tid; e < (RDP_ZCH + 2) * PLANE; e += RDP_TX * RDP_TY) {
+    const int lz = e / PLANE, rem = e % PLANE;
+    const int ly = rem / (RDP_TX + 2), lx = rem % (RDP_TX + 2);
+    const int z = z0 + lz - 1, gx = x0 + lx - 1, gy = y0 + ly - 1;
+    float v = 0.f, kv = 0.f;
+    if (z >= 0 && z < a.nz && gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny) {
+      const size_t gi = (size_t)z * nxy + (size_t)gy * a.nx + gx;
+      v = __ldg(x + gi);
+      if (KAPPA) kv = __ldg(a.kappa + gi);
     }
-  };
-
+    sx[lz][ly][lx] = v;
+    if (KAPPA) sk[lz][ly][lx] = kv;
+  }
+  __syncthreads();
   double vsum = 0.0;
-  load_plane(z0 - 1);
-  load_plane(z0);
   const int gx = x0 + tx, gy = y0 + ty;
-  for (int z = z0; z < z1; ++z) {
-    load_plane(z + 1);
-    __syncthreads();
-    if (gx < a.nx && gy < a.ny) {
+  if (gx < a.nx && gy < a.ny) {
+    for (int z = z0; z < z1; ++z) {
+      const int lz = z - z0 + 1;
       float gsum = 0.f, hsum = 0.f, vs = 0.f;
       if (inner_xy && z >= 1 && z + 1 < a.nz)
-        rdp_voxel<KAPPA, WG, WH, VAL, false>(a, sx, sk, z, gx, gy, tx, ty, gsum, hsum, vs);
+        rdp_voxel<KAPPA, WG, WH, VAL, false>(a, sx, sk, z, lz, gx, gy, tx, ty, gsum, hsum, vs);
       else
-        rdp_voxel<KAPPA, WG, WH, VAL, true>(a, sx, sk, z, gx, gy, tx, ty, gsum, hsum, vs);
+        rdp_voxel<KAPPA, WG, WH, VAL, true>(a, sx, sk, z, lz, gx, gy, tx, ty, gsum, hsum, vs);
       const size_t gi = (size_t)z * nxy + (size_t)gy * a.nx + gx;
       if (WG) grad[gi] = accumulate ? fmaf(a.scale, gsum, grad[gi]) : a.scale * gsum;
       if (WH) hdiag[gi] = a.scale * hsum;
       if (VAL) vsum += 0.5 * (double)vs;
     }
-    __syncthreads();
   }
   if (VAL) {
     const double s = block_sum_d(vsum * (double)a.scale);
