@@ -25,6 +25,7 @@ _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 
 STEP_CONST, STEP_VANISH, STEP_ALG1, STEP_BB, STEP_ALG2 = 0, 1, 2, 3, 4
 SGD, SAGA, SVRG = 0, 1, 2
+SAMPLE_PERM, SAMPLE_REPLACE, SAMPLE_HM, SAMPLE_COFACTOR, SAMPLE_IMPORTANCE = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -57,6 +58,8 @@ class _Opts(C.Structure):
         ("beta", C.c_double), ("gamma", C.c_double), ("eps", C.c_double),
         ("kappa", C.POINTER(C.c_double)),
         ("order", C.POINTER(C.c_int)),
+        ("sampling", C.c_int), ("sample_seed", C.c_uint64),
+        ("subsets_out", C.POINTER(C.c_int)),
     ]
 
 
@@ -75,6 +78,7 @@ def lib():
         _lib.o_step_alg1.restype = C.c_double
         _lib.o_step_alg2.restype = C.c_double
         _lib.o_splitmix64.restype = C.c_uint64
+        _lib.o_splitmix64_at.restype = C.c_uint64
     return _lib
 
 
@@ -230,10 +234,29 @@ def splitmix64_stream(seed, count):
     return [lib().o_splitmix64(C.byref(st)) for _ in range(count)]
 
 
-def subset_order(seed, nsub, niter):
+def subset_order(seed, nsub, niter, kind=SAMPLE_PERM):
+    """Subset per iteration under a sampling rule of Sec. 2.4 (not importance)."""
     out = np.zeros(niter, np.int32)
-    lib().o_subset_order(C.c_uint64(seed), nsub, niter, _i(out))
+    if kind == SAMPLE_PERM:
+        lib().o_subset_order(C.c_uint64(seed), nsub, niter, _i(out))
+    elif lib().o_subset_order_kind(kind, C.c_uint64(seed), nsub, niter, _i(out)) != 0:
+        raise ValueError(f"no precomputed order for sampling rule {kind}")
     return out
+
+
+def splitmix64_at(seed, k):
+    return lib().o_splitmix64_at(C.c_uint64(seed), C.c_long(k))
+
+
+def cofactor_generators(n):
+    out = np.zeros(max(n, 1), np.int32)
+    c = lib().o_cofactor_generators(n, _i(out))
+    return out[:c].copy()
+
+
+def draw_index(p, u):
+    p = _f64(p)
+    return lib().o_draw_index(_d(p), len(p), C.c_double(u))
 
 
 def step_alg1(k):
@@ -247,8 +270,11 @@ def step_alg2(k, nsub, tau_bb):
 def solve(G: Geometry, x0, m, r, y, sens, *, algo, nsub, niter, order, omega=2,
           step_rule=STEP_VANISH, tau0=1.0, eta=0.02, precond_kind=1, alpha=1.0,
           delta_rel=1e-6, pc_iters=(0,), beta=0.1, gamma=2.0, eps=1e-3, kappa=None,
-          snap_every=0):
-    """Runs SGD/SAGA/SVRG (eq. 6-9, Algorithm 1) from x0; returns (x, taus, snaps)."""
+          snap_every=0, sampling=SAMPLE_PERM, sample_seed=0, subsets_out=None):
+    """Runs SGD/SAGA/SVRG (eq. 6-9, Algorithm 1) from x0; returns (x, taus, snaps).
+    With sampling=SAMPLE_IMPORTANCE (SVRG) the subsets are drawn inside from
+    sample_seed and `order` is ignored; subsets_out (int32 array of length niter, may
+    be None) receives the subset of every iteration (-1 at snapshot refreshes)."""
     x = _f64(x0).copy()
     m, r, y, sens = _f64(m), _f64(r), _f64(y), _f64(sens)
     order = np.ascontiguousarray(order, np.int32)
@@ -256,7 +282,8 @@ def solve(G: Geometry, x0, m, r, y, sens, *, algo, nsub, niter, order, omega=2,
     kap = _f64(kappa) if kappa is not None else None
     o = _Opts(algo, nsub, niter, omega, step_rule, tau0, eta, precond_kind, alpha, delta_rel,
               pcs.ctypes.data_as(C.POINTER(C.c_long)), len(pcs), beta, gamma, eps,
-              _d(kap) if kap is not None else None, _i(order))
+              _d(kap) if kap is not None else None, _i(order), sampling, C.c_uint64(sample_seed),
+              _i(subsets_out) if subsets_out is not None else None)
     taus = np.zeros(niter)
     nsnap = niter // snap_every if snap_every > 0 else 0
     snaps = np.zeros((max(nsnap, 1),) + x.shape)

@@ -401,6 +401,118 @@ void o_subset_order(uint64_t seed, int nsub, int niter, int *order) {
 }
 
 /* ------------------------------------------------------------------------- */
+/* Subset sampling rules of Sec. 2.4.                                          */
+/* ------------------------------------------------------------------------- */
+enum { O_SAMPLE_PERM = 0, O_SAMPLE_REPLACE = 1, O_SAMPLE_HM = 2, O_SAMPLE_COFACTOR = 3,
+       O_SAMPLE_IMPORTANCE = 4 };
+
+/* Output number k (0-based) of the splitmix64 stream started at state seed, i.e.
+ * the value of the (k+1)-th call of o_splitmix64. */
+uint64_t o_splitmix64_at(uint64_t seed, long k) {
+  uint64_t st = seed;
+  uint64_t z = 0;
+  for (long c = 0; c <= k; c++) z = o_splitmix64(&st);
+  return z;
+}
+
+/* Herman-Meyer order: n = p1 p2 ... pm with the prime factors ascending; iteration j
+ * of an epoch writes j in mixed radix with digit d1 (base p1) least significant,
+ * then d2 (base p2), ..., and visits subset d1 n/p1 + d2 n/(p1 p2) + ... +
+ * dm n/(p1...pm).  For n = 2^m this is the bit reversal of j. */
+static void herman_meyer(int n, int *out) {
+  int f[64], m = 0, r = n;
+  for (int q = 2; q <= r; q++)
+    while (r % q == 0) { f[m++] = q; r /= q; }
+  for (int j = 0; j < n; j++) {
+    int rest = j, w = n, idx = 0;
+    for (int t = 0; t < m; t++) {
+      w /= f[t];
+      idx += (rest % f[t]) * w;
+      rest /= f[t];
+    }
+    out[j] = idx;
+  }
+}
+
+static int gcd_int(int a, int b) {
+  while (b) { int t = a % b; a = b; b = t; }
+  return a;
+}
+
+/* Cofactor order: the generators of the cyclic group Z_n (1 <= g < n, gcd(g, n) = 1)
+ * ranked by their distance to the nearer of 0.3 n and 0.7 n (ties: smaller g first;
+ * distances compared as the integers |10 g - 3 n|, |10 g - 7 n|).  Epoch e uses the
+ * (e mod count)-th generator g and visits 0, g, 2g, ... (mod n).  Returns the number
+ * of generators written to gens (n - 1 at most). */
+int o_cofactor_generators(int n, int *gens) {
+  int c = 0;
+  for (int g = 1; g < n; g++)
+    if (gcd_int(g, n) == 1) gens[c++] = g;
+  for (int a = 1; a < c; a++) { /* insertion sort by (distance, g) */
+    int g = gens[a], b = a - 1;
+    int dg = abs(10 * g - 3 * n) < abs(10 * g - 7 * n) ? abs(10 * g - 3 * n) : abs(10 * g - 7 * n);
+    while (b >= 0) {
+      int h = gens[b];
+      int dh = abs(10 * h - 3 * n) < abs(10 * h - 7 * n) ? abs(10 * h - 3 * n) : abs(10 * h - 7 * n);
+      if (dh < dg || (dh == dg && h < g)) break;
+      gens[b + 1] = h;
+      b--;
+    }
+    gens[b + 1] = g;
+  }
+  return c;
+}
+
+/* Subset index for each of niter iterations under the rules of Sec. 2.4:
+ *   O_SAMPLE_PERM      uniformly at random without replacement (o_subset_order);
+ *   O_SAMPLE_REPLACE   uniformly at random with replacement: iteration k takes
+ *                      ((z_k >> 32) n) >> 32 with z_k = o_splitmix64_at(seed, k);
+ *   O_SAMPLE_HM        Herman-Meyer order, repeated every epoch;
+ *   O_SAMPLE_COFACTOR  cofactor order (o_cofactor_generators).
+ * Returns 0, or -1 for an unknown kind (importance sampling depends on the iterates
+ * and is drawn inside o_solve). */
+int o_subset_order_kind(int kind, uint64_t seed, int nsub, int niter, int *order) {
+  if (kind == O_SAMPLE_PERM) { o_subset_order(seed, nsub, niter, order); return 0; }
+  if (kind == O_SAMPLE_REPLACE) {
+    uint64_t st = seed;
+    for (int k = 0; k < niter; k++) order[k] = (int)(((o_splitmix64(&st) >> 32) * (uint64_t)nsub) >> 32);
+    return 0;
+  }
+  if (kind == O_SAMPLE_HM) {
+    int *hm = malloc(sizeof(int) * nsub);
+    herman_meyer(nsub, hm);
+    for (int k = 0; k < niter; k++) order[k] = hm[k % nsub];
+    free(hm);
+    return 0;
+  }
+  if (kind == O_SAMPLE_COFACTOR) {
+    int *gens = malloc(sizeof(int) * (nsub > 1 ? nsub : 1));
+    int c = o_cofactor_generators(nsub, gens);
+    for (int k = 0; k < niter; k++) {
+      int e = k / nsub, j = k % nsub;
+      int g = c > 0 ? gens[e % c] : 0;
+      order[k] = (int)(((long)j * g) % nsub);
+    }
+    free(gens);
+    return 0;
+  }
+  return -1;
+}
+
+/* Importance draw (Sec. 2.4): the smallest i with u < p_0 + ... + p_i (cumulative sum in
+ * index order, FP64), or the last i with p_i > 0 when rounding leaves u above the sum. */
+int o_draw_index(const double *p, int n, double u) {
+  double c = 0.0;
+  int last = 0;
+  for (int i = 0; i < n; i++) {
+    if (p[i] > 0) last = i;
+    c += p[i];
+    if (p[i] > 0 && u < c) return i;
+  }
+  return last;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Stepsize rules, Sec. 2.2 and Table 1.                                       */
 /* ------------------------------------------------------------------------- */
 enum { O_STEP_CONST = 0, O_STEP_VANISH = 1, O_STEP_ALG1 = 2, O_STEP_BB = 3, O_STEP_ALG2 = 4 };
@@ -439,6 +551,9 @@ typedef struct {
   double beta, gamma, eps;         /* RDP */
   const double *kappa;             /* may be NULL */
   const int *order;                /* subset index per iteration (length niter) */
+  int sampling;                    /* O_SAMPLE_IMPORTANCE draws inside (SVRG); else order */
+  uint64_t sample_seed;            /* importance draws: u_k from o_splitmix64_at(seed, k) */
+  int *subsets_out;                /* may be NULL: subset used by each non-refresh iteration */
 } og_opts;
 
 /* Gradient of f_i at x: data gradient of subset i plus (beta/n) grad S. */
@@ -474,6 +589,11 @@ int o_solve(const og_geom *g, const og_opts *o, const double *m, const double *r
   }
   int have_bb = 0, have_snapshot = 0;
   double tau_bb = o->tau0;
+  /* importance sampling (Sec. 2.4, SVRG): p_i proportional to ||grad f_i(xhat)||,
+   * recomputed at every snapshot refresh */
+  const int importance = o->algo == 2 && o->sampling == O_SAMPLE_IMPORTANCE;
+  double *prob = malloc(sizeof(double) * n);
+  for (int i = 0; i < n; i++) prob[i] = 1.0 / n;
   /* SAGA table initialisation: all g_i = grad f_i(x^0) (a reading; the paper is
    * silent).  It takes no step. */
   if (o->algo == 1) {
@@ -496,12 +616,15 @@ int o_solve(const og_geom *g, const og_opts *o, const double *m, const double *r
         }
         o_precond(N, o->precond_kind, x, sens, H, o->alpha, delta, D);
       }
+    if (o->subsets_out) o->subsets_out[k] = -1; /* refresh iterations use no subset */
     if (o->algo == 0) { /* SGD: n grad f_i */
       int i = o->order[k];
+      if (o->subsets_out) o->subsets_out[k] = i;
       subset_objective_grad(g, o, i, x, m, rr, y, gi, tmp);
       for (size_t v = 0; v < N; v++) dir[v] = n * gi[v];
     } else if (o->algo == 1) { /* SAGA, eq. 7 */
       int i = o->order[k];
+      if (o->subsets_out) o->subsets_out[k] = i;
       subset_objective_grad(g, o, i, x, m, rr, y, gi, tmp);
       double *Ti = table + (size_t)i * N;
       for (size_t v = 0; v < N; v++) {
@@ -530,12 +653,32 @@ int o_solve(const og_geom *g, const og_opts *o, const double *m, const double *r
         memcpy(xhat_old, x, sizeof(double) * N);
         memcpy(G_old, G, sizeof(double) * N);
         have_snapshot = 1;
+        if (importance) {
+          double tot = 0.0;
+          for (int i = 0; i < n; i++) {
+            double s2 = 0.0;
+            for (size_t v = 0; v < N; v++) s2 += table[(size_t)i * N + v] * table[(size_t)i * N + v];
+            prob[i] = sqrt(s2);
+            tot += prob[i];
+          }
+          for (int i = 0; i < n; i++) prob[i] = tot > 0 ? prob[i] / tot : 1.0 / n;
+        }
         for (size_t v = 0; v < N; v++) dir[v] = G[v];
       } else {
-        int i = o->order[k];
+        int i;
+        double w = n; /* uniform sampling: 1/p_i = n */
+        if (importance) {
+          /* with probabilities p the unbiased estimator weights the correction by 1/p_i */
+          double u = (double)(o_splitmix64_at(o->sample_seed, k) >> 11) * (1.0 / 9007199254740992.0);
+          i = o_draw_index(prob, n, u);
+          w = 1.0 / prob[i];
+        } else {
+          i = o->order[k];
+        }
+        if (o->subsets_out) o->subsets_out[k] = i;
         subset_objective_grad(g, o, i, x, m, rr, y, gi, tmp);
         double *Ti = table + (size_t)i * N;
-        for (size_t v = 0; v < N; v++) dir[v] = n * (gi[v] - Ti[v]) + G[v];
+        for (size_t v = 0; v < N; v++) dir[v] = w * (gi[v] - Ti[v]) + G[v];
       }
     }
     double tau;
@@ -558,6 +701,7 @@ int o_solve(const og_geom *g, const og_opts *o, const double *m, const double *r
     }
   }
   (void)have_bb;
+  free(prob);
   free(D); free(dir); free(gi); free(tmp); free(H);
   free(table); free(G); free(xhat_old); free(G_old);
   return 0;
