@@ -46,6 +46,7 @@ class _Geom(C.Structure):
         ("drad", C.c_double), ("rdet", C.c_double),
         ("z1", C.POINTER(C.c_double)), ("z2", C.POINTER(C.c_double)),
         ("tof_sigma", C.c_double), ("tof_bin", C.c_double),
+        ("res_fwhm", C.c_double),
     ]
 
 
@@ -98,7 +99,8 @@ class Geometry:
     """Holds a C geometry struct plus the arrays it points to.
 
     ``geom`` is a mapping with keys nx, ny, nz, dx, dy, dz, nrad, nview, drad, rdet,
-    z1, z2 (per-plane endpoint axial positions, mm), ntof, tof_sigma, tof_bin.
+    z1, z2 (per-plane endpoint axial positions, mm), ntof, tof_sigma, tof_bin and
+    optionally res_fwhm (image-space Gaussian resolution model, mm; default none).
     """
 
     def __init__(self, geom):
@@ -109,7 +111,8 @@ class Geometry:
                        float(geom["dx"]), float(geom["dy"]), float(geom["dz"]),
                        int(geom["nrad"]), int(geom["nview"]), len(self.z1), self.ntof,
                        float(geom["drad"]), float(geom["rdet"]), _d(self.z1), _d(self.z2),
-                       float(geom.get("tof_sigma", 1.0)), float(geom.get("tof_bin", 1.0)))
+                       float(geom.get("tof_sigma", 1.0)), float(geom.get("tof_bin", 1.0)),
+                       float(geom.get("res_fwhm", 0.0)))
         g = self.s
         self.img_shape = (g.nz, g.ny, g.nx)
         self.T = self.ntof if self.ntof > 1 else 1
@@ -119,6 +122,16 @@ class Geometry:
     @property
     def ref(self):
         return C.byref(self.s)
+
+
+def gauss_filter(x, spacing, fwhm):
+    """G x: separable Gaussian of the given FWHM (mm), zero outside the image."""
+    x = _f64(x)
+    out = np.empty_like(x)
+    nz, ny, nx = x.shape
+    lib().o_gauss_filter(nx, ny, nz, C.c_double(spacing[0]), C.c_double(spacing[1]), C.c_double(spacing[2]),
+                         C.c_double(fwhm), _d(x), _d(out))
+    return out
 
 
 def subset_views(nview, nsub, s):

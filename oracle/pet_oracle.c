@@ -41,7 +41,75 @@ typedef struct {
   const double *z1, *z2; /* per plane: axial position (mm) of endpoint 1 and 2 */
   double tof_sigma;      /* TOF Gaussian sigma along the LOR (mm) */
   double tof_bin;        /* TOF bin width (mm) */
+  double res_fwhm;       /* image-space Gaussian resolution model, FWHM (mm); 0 = none */
 } og_geom;
+
+/* ------------------------------------------------------------------------- */
+/* Image-space resolution model (Sec. 3.1: an isotropic Gaussian kernel of     */
+/* 4 mm models the limited spatial resolution): P is replaced by P G, where G  */
+/* convolves with a Gaussian of the given FWHM, sigma = FWHM / (2 sqrt(2 ln 2)). */
+/* Per axis the kernel is sampled at the voxel offsets k*delta, |k| <= R =     */
+/* ceil(3 sigma / delta), and normalised to unit sum; voxels outside the image */
+/* count as zero.  The axial pass is skipped for single-slice images.  With a  */
+/* symmetric kernel and zero padding, G is its own adjoint, so the            */
+/* backprojector applies the same G after P^T.                                 */
+/* ------------------------------------------------------------------------- */
+static int gauss_taps(double fwhm, double delta, double *w) {
+  double sigma = fwhm / (2.0 * sqrt(2.0 * log(2.0)));
+  int R = (int)ceil(3.0 * sigma / delta);
+  double sum = 0.0;
+  for (int k = -R; k <= R; k++) {
+    w[k + R] = exp(-(k * delta) * (k * delta) / (2.0 * sigma * sigma));
+    sum += w[k + R];
+  }
+  for (int k = 0; k <= 2 * R; k++) w[k] /= sum;
+  return R;
+}
+
+/* out = G in (out may not alias in). */
+void o_gauss_filter(int nx, int ny, int nz, double dx, double dy, double dz, double fwhm,
+                    const double *in, double *out) {
+  size_t N = (size_t)nx * ny * nz;
+  if (!(fwhm > 0)) { memcpy(out, in, sizeof(double) * N); return; }
+  int n[3] = {nx, ny, nz};
+  double del[3] = {dx, dy, dz};
+  size_t stride[3] = {1, (size_t)nx, (size_t)nx * ny};
+  double *a = malloc(sizeof(double) * N), *b = malloc(sizeof(double) * N);
+  memcpy(a, in, sizeof(double) * N);
+  for (int ax = 0; ax < 3; ax++) {
+    if (ax == 2 && nz == 1) continue;
+    int Rmax = (int)ceil(3.0 * fwhm / (2.0 * sqrt(2.0 * log(2.0))) / del[ax]);
+    double *w = malloc(sizeof(double) * (2 * Rmax + 1));
+    int R = gauss_taps(fwhm, del[ax], w);
+    for (int iz = 0; iz < nz; iz++)
+      for (int iy = 0; iy < ny; iy++)
+        for (int ix = 0; ix < nx; ix++) {
+          int i3[3] = {ix, iy, iz};
+          size_t c = (size_t)iz * stride[2] + (size_t)iy * stride[1] + ix;
+          double acc = 0.0;
+          for (int k = -R; k <= R; k++) {
+            int j = i3[ax] + k;
+            if (j < 0 || j >= n[ax]) continue;
+            acc += w[k + R] * a[c + (long)k * (long)stride[ax]];
+          }
+          b[c] = acc;
+        }
+    free(w);
+    double *t = a; a = b; b = t;
+  }
+  memcpy(out, a, sizeof(double) * N);
+  free(a); free(b);
+}
+
+/* x itself, or G x in a new buffer (to be freed) when the geometry has a resolution model. */
+static const double *resolved_input(const og_geom *g, const double *x, double **owned) {
+  *owned = NULL;
+  if (!(g->res_fwhm > 0)) return x;
+  size_t N = (size_t)g->nx * g->ny * g->nz;
+  *owned = malloc(sizeof(double) * N);
+  o_gauss_filter(g->nx, g->ny, g->nz, g->dx, g->dy, g->dz, g->res_fwhm, x, *owned);
+  return *owned;
+}
 
 /* LOR endpoints on the detector cylinder.  View v has angle v*pi/V, radial bin r
  * sits at signed distance s=(r-(R-1)/2)*drad from the axis, the in-plane
@@ -156,7 +224,9 @@ int o_subset_views(int nview, int nsub, int s, int *views) {
 
 /* Geometric projection P x over the listed views (no multiplicative factors):
  * out[j][p][r][b] for j over the listed views. Returns 0 or -1 (bad geometry). */
-int o_project(const og_geom *g, const int *views, int nviews, const double *x, double *out) {
+int o_project(const og_geom *g, const int *views, int nviews, const double *x_in, double *out) {
+  double *owned;
+  const double *x = resolved_input(g, x_in, &owned);
   int me = max_entries(g);
   int *vox = malloc(sizeof(int) * me);
   double *wt = malloc(sizeof(double) * me), *tp = malloc(sizeof(double) * me);
@@ -177,12 +247,14 @@ int o_project(const og_geom *g, const int *views, int nviews, const double *x, d
           o[b] = acc;
         }
       }
-  free(vox); free(wt); free(tp);
+  free(vox); free(wt); free(tp); free(owned);
   return rc;
 }
 
 /* Geometric projection of an explicit list of LORs (v, p, r triples): out[l][b]. */
-int o_project_lors(const og_geom *g, const int *vpr, int nl, const double *x, double *out) {
+int o_project_lors(const og_geom *g, const int *vpr, int nl, const double *x_in, double *out) {
+  double *owned;
+  const double *x = resolved_input(g, x_in, &owned);
   int me = max_entries(g);
   int *vox = malloc(sizeof(int) * me);
   double *wt = malloc(sizeof(double) * me), *tp = malloc(sizeof(double) * me);
@@ -200,7 +272,7 @@ int o_project_lors(const og_geom *g, const int *vpr, int nl, const double *x, do
       out[(size_t)l * T + b] = acc;
     }
   }
-  free(vox); free(wt); free(tp);
+  free(vox); free(wt); free(tp); free(owned);
   return rc;
 }
 
@@ -225,6 +297,12 @@ int o_backproject(const og_geom *g, const int *views, int nviews, const double *
             img[vox[e]] += wt[e] * tw * qq[b];
           }
       }
+  if (g->res_fwhm > 0) { /* (P G)^T = G P^T */
+    double *t = malloc(sizeof(double) * N);
+    o_gauss_filter(g->nx, g->ny, g->nz, g->dx, g->dy, g->dz, g->res_fwhm, img, t);
+    memcpy(img, t, sizeof(double) * N);
+    free(t);
+  }
   free(vox); free(wt); free(tp);
   return rc;
 }
@@ -237,6 +315,7 @@ int o_multiplicative(const og_geom *g, const double *mu, const double *sens, dou
   size_t nl = (size_t)g->nview * g->nplane * g->nrad;
   og_geom g1 = *g;
   g1.ntof = 1;
+  g1.res_fwhm = 0.0; /* attenuation: line integrals of mu through the object itself */
   int rc = 0;
   if (mu) {
     int *views = malloc(sizeof(int) * g->nview);
