@@ -44,10 +44,14 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-nrmse", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--mode", default="step", choices=["step", "grad", "c4", "c5"],
-                    help="grad: only the fused subset-gradient op, for profiler captures")
+    ap.add_argument("--mode", default="step", choices=["step", "grad", "configs", "study", "c4", "c5"],
+                    help="grad: only the fused subset-gradient op, for profiler captures; "
+                         "configs: SVRG outer-loop rates on the 2D, 3D and 3D TOF workloads; "
+                         "study: epochs to 1%% NRMSE over algorithm x preconditioner x tau0 (2D)")
     ap.add_argument("--shape", default="auto",
                     help="grad mode: 'auto' (autotuner) or 'K,S' planes per thread, parts per LOR")
+    ap.add_argument("--config", default="c2", choices=["c2", "c3"],
+                    help="grad mode: c2 (non-TOF, 1e7 counts) or c3 (11 TOF bins, 1e6 counts)")
     return ap.parse_args()
 
 
@@ -249,6 +253,124 @@ def time_to_nrmse(pet, dev, config, seed=0, threshold=0.01, max_epochs=3000):
     return out
 
 
+def svrg_loop_rate(pet, dev, p, steps, warmup, use_graph=True):
+    """Subset gradients per second of whole SVRG outer loops (refresh + 2n - 1 inner
+    iterations, harmonic preconditioner updated at each loop start), L2 flushed between
+    loops, and the average duration of the fused subset-gradient kernel."""
+    import torch
+    n = p["nsub"]
+    plan = pet.Plan(p["geom"], n)
+    y = p["y"].view(np.int16) if p["y"].dtype == np.uint16 else p["y"].astype(np.int32)
+    keep = [torch.from_numpy(y).to(dev), torch.from_numpy(p["r"]).to(dev),
+            torch.from_numpy(p["mu"].astype(np.float32)).to(dev),
+            torch.from_numpy(p["sens"].astype(np.float32)).to(dev)]
+    plan.set_data(*keep)
+    shape = plan.autotune()
+    x0 = torch.ones(plan.img_shape, device=dev)
+    for s in range(n):
+        plan.em_update(x0, s)
+    step_len = 2 * n
+    pcs = [k * step_len for k in range(steps + warmup + 1)]
+    solver = pet.Solver(plan, algo=pet.SVRG, omega=2, step_rule=pet.STEP_VANISH, tau0=1.0, eta=0.02,
+                        precond_kind=1, pc_iters=pcs, beta=p["beta"], gamma=p["gamma"], eps=p["eps"],
+                        seed=4321, use_graph=use_graph)
+    solver.set_image(x0)
+    solver.profile(True)
+    flush = torch.empty(64 * 1024 * 1024, device=dev)
+    for _ in range(warmup):
+        solver.run(step_len)
+    torch.cuda.synchronize()
+    solver.kernel_time()
+    total = 0.0
+    kms, kn = 0.0, 0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        solver.run(step_len)
+        b.record()
+        torch.cuda.synchronize()
+        total += a.elapsed_time(b) / 1e3
+        ms, nl = solver.kernel_time()
+        kms += ms
+        kn += nl
+    units = (3 * n - 1) * steps
+    return {"subset_grads_per_s": units / total, "ms_per_outer_loop": 1e3 * total / steps,
+            "fused_kernel_ms": kms / max(kn, 1), "grad_shape": list(shape), "graph": use_graph}
+
+
+def run_configs(args, pet, dev):
+    """Rates on the 2D (c1), 3D non-TOF (c2) and 3D TOF (c3) workloads with the roofline
+    figures of the fused subset gradient (algorithmic bytes per launch / launch time)."""
+    from paper_2506_04976_gb300 import synth
+    peak, peak_kind = measured_peaks()
+    out = {"mode": "configs", "peak_gbs": peak, "peak_kind": peak_kind, "configs": {}}
+    for cfg in ("c1", "c2", "c3"):
+        p = synth.make_problem(cfg, 0)
+        r = svrg_loop_rate(pet, dev, p, args.steps, args.warmup)
+        g = p["geom"]
+        T = g["ntof"] if g["ntof"] > 1 else 1
+        lors = (g["nview"] // p["nsub"]) * len(g["z1"]) * g["nrad"]
+        N = g["nx"] * g["ny"] * g["nz"]
+        abytes = lors * T * (p["y"].itemsize + 4) + lors * 4 + 2 * 4 * N
+        r["algorithmic_bytes"] = abytes
+        r["achieved_gbs"] = abytes / (r["fused_kernel_ms"] * 1e-3) / 1e9
+        r["hbm_frac"] = r["achieved_gbs"] / peak
+        if T > 1:
+            r["tof_bins_per_s"] = lors * T / (r["fused_kernel_ms"] * 1e-3)
+        out["configs"][cfg] = r
+    print(json.dumps(out), flush=True)
+
+
+def run_study(args, pet, dev, max_epochs=1500):
+    """The comparison of Sec. 3.2 (Fig. 2) on the 2D workload against its converged oracle
+    image: SGD / SAGA / SVRG x MLEM / harmonic preconditioner x tau0 in {0.3, 1, 1.5},
+    vanishing steps (eta = 0.02), preconditioner updated in epochs 1-3, subsets without
+    replacement; epochs and GPU seconds from the OSEM start to NRMSE < 1%."""
+    import torch
+    from paper_2506_04976_gb300 import synth
+    ref_path = os.path.join(ROOT, "tests", "golden", "ref_c1_seed0.npz")
+    ref = np.load(ref_path)
+    p = synth.make_problem("c1", 0)
+    n = p["nsub"]
+    plan = pet.Plan(p["geom"], n)
+    plan.set_data(torch.from_numpy(p["y"].astype(np.int32)).to(dev), torch.from_numpy(p["r"]).to(dev),
+                  torch.from_numpy(p["mu"].astype(np.float32)).to(dev),
+                  torch.from_numpy(p["sens"].astype(np.float32)).to(dev))
+    xref = torch.from_numpy(ref["x"]).to(dev)
+    mask = torch.from_numpy(p["mask"]).to(dev)
+    bg = torch.from_numpy(p["bg"]).to(dev)
+    x0 = torch.ones(plan.img_shape, device=dev)
+    for s in range(n):
+        plan.em_update(x0, s)
+    rows = []
+    for algo, aname in ((pet.SGD, "SGD"), (pet.SAGA, "SAGA"), (pet.SVRG, "SVRG")):
+        for pc, pname in ((0, "MLEM"), (1, "harmonic")):
+            for tau0 in (0.3, 1.0, 1.5):
+                solver = pet.Solver(plan, algo=algo, omega=2, step_rule=pet.STEP_VANISH, tau0=tau0, eta=0.02,
+                                    precond_kind=pc, pc_iters=(0, n, 2 * n), beta=p["beta"], gamma=p["gamma"],
+                                    eps=p["eps"], seed=31)
+                solver.set_image(x0)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                reached, val = None, None
+                for e in range(1, max_epochs + 1):
+                    solver.run(n)
+                    val = float(pet.nrmse(solver.image(), xref, mask, bg))
+                    if not np.isfinite(val):
+                        break
+                    if val < 0.01:
+                        reached = e
+                        break
+                b.record()
+                torch.cuda.synchronize()
+                rows.append({"algo": aname, "precond": pname, "tau0": tau0, "epochs_to_1pct": reached,
+                             "seconds": a.elapsed_time(b) / 1e3, "final_nrmse": val})
+    print(json.dumps({"mode": "study", "workload": "c1 (2D, n = 6, beta = 0.1)", "max_epochs": max_epochs,
+                      "reference_kkt": float(ref["kkt"]), "runs": rows}), flush=True)
+
+
 def run_batched(args, pet, dev, E=8):
     """32 independent reconstructions of uneven size (c4): SAGA with harmonic
     preconditioner, advanced by the batched driver (one launch per phase, one graph
@@ -364,16 +486,18 @@ def run_c5(args, pet, dev):
 def run_grad_only(args, pet, dev):
     """Subset gradients only (objective_grad on successive subsets), for ncu captures."""
     import torch
-    p = make_inputs(0)
+    from paper_2506_04976_gb300 import synth
+    p = synth.make_problem(args.config, 0)
     plan = pet.Plan(p["geom"], p["nsub"])
-    plan.set_data(torch.from_numpy(p["y"].view(np.int16)).to(dev), torch.from_numpy(p["r"]).to(dev),
+    y = p["y"].view(np.int16) if p["y"].dtype == np.uint16 else p["y"].astype(np.int32)
+    plan.set_data(torch.from_numpy(y).to(dev), torch.from_numpy(p["r"]).to(dev),
                   torch.from_numpy(p["mu"].astype(np.float32)).to(dev),
                   torch.from_numpy(p["sens"].astype(np.float32)).to(dev))
     if args.shape == "auto":
-        plan.autotune()
+        shape = plan.autotune()
     else:
-        k, sp = (int(v) for v in args.shape.split(","))
-        plan.set_grad_shape(k, sp)
+        shape = tuple(int(v) for v in args.shape.split(","))
+        plan.set_grad_shape(*shape)
     x = torch.from_numpy(np.maximum(p["x_true"], 0.05 * p["x_true"].max()).astype(np.float32)).to(dev)
     gbuf = torch.empty_like(x)
     for i in range(args.warmup):
@@ -385,7 +509,8 @@ def run_grad_only(args, pet, dev):
         plan.objective_grad(x, i % p["nsub"], g=gbuf, want_obj=False)
     b.record()
     torch.cuda.synchronize()
-    print(json.dumps({"mode": "grad", "ms_per_call": a.elapsed_time(b) / max(args.steps, 1)}))
+    print(json.dumps({"mode": "grad", "config": args.config, "shape": list(shape),
+                      "ms_per_call": a.elapsed_time(b) / max(args.steps, 1)}))
 
 
 def main():
@@ -407,6 +532,10 @@ def main():
 
     if args.mode == "grad":
         return run_grad_only(args, pet, dev)
+    if args.mode == "configs":
+        return run_configs(args, pet, dev)
+    if args.mode == "study":
+        return run_study(args, pet, dev)
     if args.mode == "c4":
         return run_batched(args, pet, dev)
     if args.mode == "c5":

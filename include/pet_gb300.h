@@ -56,7 +56,11 @@ typedef struct pet_solver pet_solver;
  * ntof <= 1 means non-TOF; otherwise bin b of width tof_bin (mm) is centred at
  * (b-(ntof-1)/2)*tof_bin from the LOR midpoint toward endpoint 2 and the timing
  * kernel is a Gaussian of std tof_sigma (mm) truncated at 3 sigma.  nsubsets is the
- * number n of view subsets (eq. 2). */
+ * number n of view subsets (eq. 2).  res_fwhm > 0 adds the image-space resolution
+ * model of Sec. 3.1: the system matrix becomes P G with G a separable Gaussian of
+ * that FWHM (mm), sampled at the voxel offsets |k| <= ceil(3 sigma / delta) per axis
+ * (at most 31), normalised to unit sum, zero outside the image, no axial pass when
+ * nz = 1; the attenuation factors use P alone.  0 = no resolution model. */
 typedef struct {
   int nx, ny, nz;
   double dx, dy, dz;
@@ -65,6 +69,7 @@ typedef struct {
   const double *z1, *z2;
   double tof_sigma, tof_bin;
   int nsubsets;
+  double res_fwhm;
 } pet_geometry;
 
 /* Relative difference prior (eq. 3) parameters.  Outputs of pet_rdp are scaled by
@@ -205,6 +210,23 @@ typedef enum {
   PET_STEP_ALG2 = 4    /* BB capped at 3 / 2.2 / 1         (Table 1, ALG2/3) */
 } pet_step_rule;
 
+/* Subset sampling rules (Sec. 2.4).  z_k is output number k (0-based) of the splitmix64
+ * stream started at the solver's seed. */
+typedef enum {
+  PET_SAMPLE_PERM = 0,      /* uniformly at random without replacement: one Fisher-Yates
+                               permutation per epoch, j = z mod (i + 1) for i = n-1..1 */
+  PET_SAMPLE_REPLACE = 1,   /* uniformly at random with replacement: ((z_k >> 32) n) >> 32 */
+  PET_SAMPLE_HM = 2,        /* Herman-Meyer order (mixed-radix digit reversal over the
+                               ascending prime factors of n), the same every epoch */
+  PET_SAMPLE_COFACTOR = 3,  /* cofactor order: generators g of Z_n ranked by distance to
+                               0.3 n / 0.7 n (ties: smaller g); epoch e visits j g mod n with
+                               the (e mod count)-th generator */
+  PET_SAMPLE_IMPORTANCE = 4 /* SVRG only: p_i = ||grad f_i(xhat)|| / sum_j ||grad f_j(xhat)||
+                               at each refresh; iteration k takes the smallest i with
+                               (z_k >> 11) 2^-53 < p_0 + ... + p_i, drawn on the device, and
+                               weights the correction by 1/p_i (unbiased) */
+} pet_sampling;
+
 /* Options of the preconditioned proximal stochastic gradient method (eq. 6) with
  * the SGD, SAGA (eq. 7) or SVRG (eq. 9, Algorithm 1) estimator. */
 typedef struct {
@@ -223,6 +245,11 @@ typedef struct {
   long long norder;
   int use_graph;          /* capture each epoch in a CUDA graph */
   int deterministic;      /* deterministic backprojector */
+  int sampling;           /* pet_sampling (an explicit order overrides it, except importance) */
+  int low_memory;         /* SVRG without the [n][N] table (Sec. 2.1): each inner iteration
+                             recomputes the subset gradient at the snapshot (two fused
+                             gradients per iteration); the refresh computes the full data
+                             gradient in one pass over all views */
 } pet_solver_opts;
 
 pet_status pet_solver_create(pet_plan *plan, const pet_solver_opts *opts, pet_solver **out);
@@ -236,6 +263,9 @@ pet_status pet_solver_run(pet_solver *s, long long niter, void *stream);
 /* Host copy of the stepsizes used so far (up to cap entries); returns the count. */
 long long pet_solver_taus(const pet_solver *s, double *taus, long long cap);
 long long pet_solver_iteration(const pet_solver *s);
+/* Host copy of the subset used by each iteration so far (-1 at SVRG snapshot refreshes),
+ * up to cap entries; returns the count.  Synchronises with the device. */
+long long pet_solver_subsets(const pet_solver *s, int *subsets, long long cap);
 
 /* ---------------------------------------------------------------- batches */
 

@@ -26,6 +26,7 @@ _lib = C.CDLL(LIB_PATH)
 PET_Y_U16, PET_Y_U32, PET_Y_F32 = 0, 1, 2
 SGD, SAGA, SVRG = 0, 1, 2
 STEP_CONST, STEP_VANISH, STEP_ALG1, STEP_BB, STEP_ALG2 = 0, 1, 2, 3, 4
+SAMPLE_PERM, SAMPLE_REPLACE, SAMPLE_HM, SAMPLE_COFACTOR, SAMPLE_IMPORTANCE = 0, 1, 2, 3, 4
 GRAD_DETERMINISTIC, OBJ_ONLY = 1, 2
 
 STATUS = {0: "PET_OK", 1: "PET_ERR_ARG", 2: "PET_ERR_SHAPE", 3: "PET_ERR_INFEASIBLE",
@@ -49,6 +50,7 @@ class Geometry(C.Structure):
         ("z1", C.POINTER(C.c_double)), ("z2", C.POINTER(C.c_double)),
         ("tof_sigma", C.c_double), ("tof_bin", C.c_double),
         ("nsubsets", C.c_int),
+        ("res_fwhm", C.c_double),
     ]
 
 
@@ -72,6 +74,7 @@ class SolverOpts(C.Structure):
         ("seed", C.c_ulonglong),
         ("order", C.POINTER(C.c_int)), ("norder", C.c_longlong),
         ("use_graph", C.c_int), ("deterministic", C.c_int),
+        ("sampling", C.c_int), ("low_memory", C.c_int),
     ]
 
 
@@ -102,6 +105,7 @@ _sigs = {
     "pet_solver_run": (C.c_int, [_vp, C.c_longlong, _vp]),
     "pet_solver_taus": (C.c_longlong, [_vp, C.POINTER(C.c_double), C.c_longlong]),
     "pet_solver_iteration": (C.c_longlong, [_vp]),
+    "pet_solver_subsets": (C.c_longlong, [_vp, C.POINTER(C.c_int), C.c_longlong]),
     "pet_solver_profile": (C.c_int, [_vp, C.c_int]),
     "pet_launch_count": (C.c_longlong, []),
     "pet_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, C.POINTER(_vp)]),
@@ -166,7 +170,7 @@ class Plan:
                      self._z1.ctypes.data_as(C.POINTER(C.c_double)),
                      self._z2.ctypes.data_as(C.POINTER(C.c_double)),
                      float(geom.get("tof_sigma", 1.0)), float(geom.get("tof_bin", 1.0)),
-                     self.nsub)
+                     self.nsub, float(geom.get("res_fwhm", 0.0)))
         h = _vp()
         _ck(_lib.pet_plan_create(C.byref(g), C.byref(h)), "pet_plan_create")
         self._h = h
@@ -320,7 +324,8 @@ class Solver:
 
     def __init__(self, plan: Plan, *, algo=SVRG, omega=2, step_rule=STEP_VANISH, tau0=1.0, eta=0.02,
                  precond_kind=1, alpha=1.0, delta_rel=1e-6, pc_iters=(0,), beta=0.1, gamma=2.0,
-                 eps=1e-3, kappa=None, seed=0, order=None, use_graph=True, deterministic=False):
+                 eps=1e-3, kappa=None, seed=0, order=None, use_graph=True, deterministic=False,
+                 sampling=SAMPLE_PERM, low_memory=False):
         self.plan = plan
         self._pc = np.ascontiguousarray(pc_iters, np.int64)
         self._order = np.ascontiguousarray(order, np.int32) if order is not None else None
@@ -331,7 +336,7 @@ class Solver:
                        seed,
                        self._order.ctypes.data_as(C.POINTER(C.c_int)) if self._order is not None else None,
                        len(self._order) if self._order is not None else 0,
-                       int(bool(use_graph)), int(bool(deterministic)))
+                       int(bool(use_graph)), int(bool(deterministic)), int(sampling), int(bool(low_memory)))
         h = _vp()
         _ck(_lib.pet_solver_create(plan._h, C.byref(o), C.byref(h)), "pet_solver_create")
         self._h = h
@@ -371,6 +376,14 @@ class Solver:
         buf = (C.c_double * max(n, 1))()
         c = _lib.pet_solver_taus(self._h, buf, n)
         return np.array(buf[:c])
+
+    def subsets(self):
+        """Subset used by each iteration so far (-1 at SVRG snapshot refreshes)."""
+        torch.cuda.current_stream().synchronize()
+        n = self.k
+        buf = (C.c_int * max(n, 1))()
+        c = _lib.pet_solver_subsets(self._h, buf, n)
+        return np.array(buf[:c], dtype=np.int32)
 
 
 class Batch:

@@ -4,6 +4,8 @@
 // of Sec. 2.3 (eq. 8), the EM update and the NRMSE of Sec. 3.1.
 #include <math.h>
 
+#include <algorithm>
+
 #include "pet_internal.cuh"
 
 namespace petgb {
@@ -333,6 +335,43 @@ cudaError_t launch_nrmse(const float *x, const float *ref, const uint8_t *mask, 
   k_nrmse_part<<<nb, 256, 0, st>>>(x, ref, mask, bg, n, part);
   note_launch();
   k_nrmse_final<<<1, 32, 0, st>>>(part, nb, out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ resolution model
+// One separable pass of the image-space Gaussian along axis AXIS (0 x, 1 y, 2 z):
+// out[i] = sum_k w[k + R] in[i + k e_AXIS], neighbours outside the image omitted.
+// One thread per output voxel; consecutive threads take consecutive x, so every tap
+// is a coalesced row read (the image is L2-resident at the sizes of interest).
+template <int AXIS>
+__global__ void __launch_bounds__(256) k_gauss(const float *__restrict__ in, float *__restrict__ out, int nx,
+                                              int ny, int nz, GaussTaps t) {
+  const size_t N = (size_t)nx * ny * nz;
+  const int n = AXIS == 0 ? nx : AXIS == 1 ? ny : nz;
+  const size_t stride = AXIS == 0 ? 1 : AXIS == 1 ? (size_t)nx : (size_t)nx * ny;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    const int c = AXIS == 0 ? (int)(i % nx) : AXIS == 1 ? (int)((i / nx) % ny) : (int)(i / ((size_t)nx * ny));
+    const int k0 = max(-t.R, -c), k1 = min(t.R, n - 1 - c);
+    float acc = 0.f;
+    for (int k = k0; k <= k1; ++k) acc = fmaf(t.w[k + t.R], __ldg(in + (long long)i + (long long)k * (long long)stride), acc);
+    out[i] = acc;
+  }
+}
+
+cudaError_t launch_gauss(const GaussTaps *t, int nx, int ny, int nz, const float *in, float *out, float *tmp,
+                         cudaStream_t st) {
+  const size_t N = (size_t)nx * ny * nz;
+  const unsigned grid = (unsigned)std::min<size_t>((size_t)152 * 8, (N + 255) / 256);
+  note_launch();
+  k_gauss<0><<<grid, 256, 0, st>>>(in, tmp, nx, ny, nz, t[0]);
+  note_launch();
+  k_gauss<1><<<grid, 256, 0, st>>>(tmp, out, nx, ny, nz, t[1]);
+  if (nz > 1) {
+    note_launch();
+    k_gauss<2><<<grid, 256, 0, st>>>(out, tmp, nx, ny, nz, t[2]);
+    cudaError_t e = cudaMemcpyAsync(out, tmp, N * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "pet_internal.cuh"
@@ -60,7 +61,24 @@ static void plan_free(pet_plan *p) {
   cudaFree(p->d_fpart); cudaFree(p->d_fscalar); cudaFree(p->d_qtmp); cudaFree(p->d_img);
   cudaFree(p->d_groups); cudaFree(p->d_gzd); cudaFree(p->d_gplane); cudaFree(p->d_gzs);
   cudaFree(p->d_erfc_tab);
+  cudaFree(p->d_xs); cudaFree(p->d_rtmp);
   delete p;
+}
+
+// Taps of the resolution model along one axis of spacing delta: the Gaussian of the
+// given FWHM sampled at k delta, |k| <= ceil(3 sigma / delta), normalised to unit sum.
+static bool gauss_taps(double fwhm, double delta, GaussTaps &t) {
+  const double sigma = fwhm / (2.0 * sqrt(2.0 * log(2.0)));
+  const double Rd = ceil(3.0 * sigma / delta);
+  if (!(Rd <= kGaussMaxR)) return false;
+  t.R = (int)Rd;
+  double w[2 * kGaussMaxR + 1], sum = 0.0;
+  for (int k = -t.R; k <= t.R; ++k) {
+    w[k + t.R] = exp(-(k * delta) * (k * delta) / (2.0 * sigma * sigma));
+    sum += w[k + t.R];
+  }
+  for (int k = 0; k < 2 * kGaussMaxR + 1; ++k) t.w[k] = k <= 2 * t.R ? (float)(w[k] / sum) : 0.f;
+  return true;
 }
 
 extern "C" pet_status pet_plan_create(const pet_geometry *geom, pet_plan **out) {
@@ -73,6 +91,12 @@ extern "C" pet_status pet_plan_create(const pet_geometry *geom, pet_plan **out) 
   if (g.nsubsets < 1 || g.nsubsets > g.nview) return PET_ERR_ARG;
   if (g.ntof > 32) return PET_ERR_UNSUPPORTED;
   if (g.ntof > 1 && !(g.tof_sigma > 0 && g.tof_bin > 0)) return PET_ERR_ARG;
+  if (!(g.res_fwhm >= 0.0) || !std::isfinite(g.res_fwhm)) return PET_ERR_ARG;
+  GaussTaps taps[3] = {};
+  const bool res = g.res_fwhm > 0.0;
+  if (res && (!gauss_taps(g.res_fwhm, g.dx, taps[0]) || !gauss_taps(g.res_fwhm, g.dy, taps[1]) ||
+              (g.nz > 1 && !gauss_taps(g.res_fwhm, g.dz, taps[2]))))
+    return PET_ERR_UNSUPPORTED;
   const long long nvox = (long long)g.nx * g.ny * g.nz;
   const long long nlor = (long long)g.nview * g.nplane * g.nrad;
   if (nvox >= (1LL << 31) || nlor >= (1LL << 31)) return PET_ERR_UNSUPPORTED;
@@ -155,6 +179,9 @@ extern "C" pet_status pet_plan_create(const pet_geometry *geom, pet_plan **out) 
             dalloc(&pl->d_part, (size_t)pl->npart) == cudaSuccess && dalloc(&pl->d_err, 1) == cudaSuccess &&
             dalloc(&pl->d_fpart, (size_t)max_blocks(pl->N)) == cudaSuccess &&
             dalloc(&pl->d_fscalar, 4) == cudaSuccess;
+  pl->res = res;
+  for (int a = 0; a < 3; ++a) pl->taps[a] = taps[a];
+  if (ok && res) ok = dalloc(&pl->d_xs, pl->N) == cudaSuccess && dalloc(&pl->d_rtmp, pl->N) == cudaSuccess;
   if (!ok) { plan_free(pl); return PET_ERR_NOMEM; }
   if (cudaMemcpy(pl->d_view, view.data(), V * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(pl->d_vr, vr.data(), vr.size() * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -250,6 +277,19 @@ cudaError_t zero_accumulators(pet_plan *p, float *g, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   return cudaMemsetAsync(p->d_gT, 0, p->N * sizeof(float), st);
 }
+cudaError_t prepare_image(pet_plan *p, const float *x, const float **img, cudaStream_t st) {
+  *img = x;
+  if (p->res) {
+    cudaError_t e = launch_gauss(p->taps, p->g.nx, p->g.ny, p->g.nz, x, p->d_xs, p->d_rtmp, st);
+    if (e != cudaSuccess) return e;
+    *img = p->d_xs;
+  }
+  return to_frames(p, *img, st);
+}
+cudaError_t apply_res(pet_plan *p, float *g, cudaStream_t st) {
+  if (!p->res) return cudaSuccess;
+  return launch_gauss(p->taps, p->g.nx, p->g.ny, p->g.nz, g, g, p->d_rtmp, st);
+}
 }  // namespace petgb
 
 extern "C" pet_status pet_plan_set_data(pet_plan *plan, const void *y, pet_ytype yt, const float *r,
@@ -264,8 +304,11 @@ extern "C" pet_status pet_plan_set_data(pet_plan *plan, const void *y, pet_ytype
   PET_CK(launch_mult(dp, mu, plan->d_xT, sens_lor, plan->d_m, st));
   // sensitivity images with the deterministic backprojector (ones)
   PET_CK(launch_back_det(dp, plan->dd, -1, nullptr, plan->d_sens, 1, st));
-  for (int s = 0; s < plan->g.nsubsets; ++s)
+  PET_CK(apply_res(plan, plan->d_sens, st));
+  for (int s = 0; s < plan->g.nsubsets; ++s) {
     PET_CK(launch_back_det(dp, plan->dd, s, nullptr, plan->d_sens_sub + plan->N * (size_t)s, 1, st));
+    PET_CK(apply_res(plan, plan->d_sens_sub + plan->N * (size_t)s, st));
+  }
   PET_CK(cudaStreamSynchronize(st));
   plan->has_data = true;
   return PET_OK;
@@ -286,8 +329,9 @@ extern "C" pet_status pet_forward(pet_plan *plan, int subset, const float *x, fl
   if (!plan || !x || !out || bad_subset(plan, subset)) return PET_ERR_ARG;
   if (!plan->has_data) return PET_ERR_STATE;
   cudaStream_t st = S(stream);
-  PET_CK(to_frames(plan, x, st));
-  PET_CK(launch_forward(plan->dp, subset, x, plan->d_xT, out, st));
+  const float *img = nullptr;
+  PET_CK(prepare_image(plan, x, &img, st));
+  PET_CK(launch_forward(plan->dp, subset, img, plan->d_xT, out, st));
   return PET_OK;
 }
 
@@ -298,11 +342,13 @@ extern "C" pet_status pet_back(pet_plan *plan, int subset, const float *q, float
   cudaStream_t st = S(stream);
   if (deterministic) {
     PET_CK(launch_back_det(plan->dp, plan->dd, subset, q, g, 0, st));
+    PET_CK(apply_res(plan, g, st));
     return PET_OK;
   }
   PET_CK(zero_accumulators(plan, g, st));
   PET_CK(launch_back(plan->dp, subset, q, g, plan->d_gT, st));
   PET_CK(from_frames(plan, g, st));
+  PET_CK(apply_res(plan, g, st));
   return PET_OK;
 }
 
@@ -328,21 +374,26 @@ extern "C" pet_status pet_objective_grad(pet_plan *plan, int subset, const float
   if (prior && (prior->nx != plan->g.nx || prior->ny != plan->g.ny || prior->nz != plan->g.nz))
     return PET_ERR_ARG;
   cudaStream_t st = S(stream);
-  PET_CK(to_frames(plan, x, st));
+  const float *img = nullptr;
+  PET_CK(prepare_image(plan, x, &img, st));
   int nparts = 0;
   if (flags & PET_GRAD_DETERMINISTIC && !obj_only) {
     pet_status e = ensure_qtmp(plan, subset);
     if (e != PET_OK) return e;
     float *ax = plan->d_qtmp;
-    PET_CK(launch_forward(plan->dp, subset, x, plan->d_xT, ax, st));
+    PET_CK(launch_forward(plan->dp, subset, img, plan->d_xT, ax, st));
     nparts = ratio_blocks(plan->dp, subset);
     PET_CK(launch_ratio(plan->dp, subset, ax, ax, obj ? plan->d_part : nullptr, MODE_GRAD, st));
     PET_CK(launch_back_det(plan->dp, plan->dd, subset, ax, g, 0, st));
+    PET_CK(apply_res(plan, g, st));
   } else {
     if (!obj_only) PET_CK(zero_accumulators(plan, g, st));
-    PET_CK(launch_grad(plan->dp, subset, nullptr, x, plan->d_xT, g, plan->d_gT, obj ? plan->d_part : nullptr,
+    PET_CK(launch_grad(plan->dp, subset, nullptr, img, plan->d_xT, g, plan->d_gT, obj ? plan->d_part : nullptr,
                        obj_only ? MODE_OBJ : MODE_GRAD, &nparts, st));
-    if (!obj_only) PET_CK(from_frames(plan, g, st));
+    if (!obj_only) {
+      PET_CK(from_frames(plan, g, st));
+      PET_CK(apply_res(plan, g, st));
+    }
   }
   if (obj) PET_CK(launch_reduce_sum(plan->d_part, nparts, obj, 0, st));
   if (prior) {
@@ -359,10 +410,12 @@ extern "C" pet_status pet_em_update(pet_plan *plan, int subset, float *x, void *
   if (!plan->has_data) return PET_ERR_STATE;
   cudaStream_t st = S(stream);
   float *bp = plan->d_img;
-  PET_CK(to_frames(plan, x, st));
+  const float *img = nullptr;
+  PET_CK(prepare_image(plan, x, &img, st));
   PET_CK(zero_accumulators(plan, bp, st));
-  PET_CK(launch_grad(plan->dp, subset, nullptr, x, plan->d_xT, bp, plan->d_gT, nullptr, MODE_EM, nullptr, st));
+  PET_CK(launch_grad(plan->dp, subset, nullptr, img, plan->d_xT, bp, plan->d_gT, nullptr, MODE_EM, nullptr, st));
   PET_CK(from_frames(plan, bp, st));
+  PET_CK(apply_res(plan, bp, st));
   PET_CK(launch_em_apply(x, bp, plan->d_sens_sub + plan->N * (size_t)subset, plan->N, st));
   return PET_OK;
 }

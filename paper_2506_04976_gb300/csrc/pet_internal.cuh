@@ -191,7 +191,10 @@ void note_launch(long long n = 1);
 long long launch_count();
 
 // Projector kernels (proj_kernels.cu).  `subset` < 0 means all views.
-enum GradMode { MODE_GRAD = 0, MODE_EM = 1, MODE_OBJ = 2, MODE_SENS = 3 };
+enum GradMode { MODE_GRAD = 0, MODE_EM = 1, MODE_OBJ = 2, MODE_SENS = 3, MODE_NGRAD = 4 };
+// MODE_NGRAD backprojects -q: added to a MODE_GRAD result at another image it forms the
+// difference of two subset gradients (low-memory SVRG).
+__host__ __device__ __forceinline__ bool grad_like(int mode) { return mode == MODE_GRAD || mode == MODE_NGRAD; }
 
 cudaError_t launch_forward(const DevPlan &P, int subset, const float *x, const float *xT,
                            float *out, cudaStream_t st);
@@ -229,6 +232,17 @@ cudaError_t launch_mult(const DevPlan &P, const float *mu, const float *muT, con
                         float *m, cudaStream_t st);
 
 // Image kernels (image_kernels.cu).
+// Image-space resolution model: taps w[k + R], |k| <= R, of one axis (R = 0: identity).
+constexpr int kGaussMaxR = 31;
+struct GaussTaps {
+  int R;
+  float w[2 * kGaussMaxR + 1];
+};
+// out = G in with the per-axis taps t[0..2] (x, y, z; the z pass is skipped when nz = 1);
+// tmp is an image-sized scratch distinct from in and out (in and out may alias).
+cudaError_t launch_gauss(const GaussTaps *t, int nx, int ny, int nz, const float *in, float *out, float *tmp,
+                         cudaStream_t st);
+
 struct RdpArgs {
   int nx, ny, nz;
   float w[7];  // weights for offsets (1,0,0),(0,1,0),(0,0,1),(1,1,0),(1,0,1),(0,1,1),(1,1,1)

@@ -34,10 +34,19 @@ struct pet_plan {
   float *d_fpart = nullptr, *d_fscalar = nullptr;
   float *d_qtmp = nullptr;
   size_t qtmp_cap = 0;
+  // image-space resolution model (geometry res_fwhm > 0): taps per axis, G x and a temp
+  bool res = false;
+  petgb::GaussTaps taps[3];
+  float *d_xs = nullptr, *d_rtmp = nullptr;
 };
 
 namespace petgb {
 cudaError_t to_frames(pet_plan *p, const float *x, cudaStream_t st);
 cudaError_t from_frames(pet_plan *p, float *g, cudaStream_t st);
 cudaError_t zero_accumulators(pet_plan *p, float *g, cudaStream_t st);
+// The image the projector reads: x itself, or G x in plan scratch with the resolution
+// model; either way the transposed copy in d_xT is refreshed.
+cudaError_t prepare_image(pet_plan *p, const float *x, const float **img, cudaStream_t st);
+// g <- G g when the plan has a resolution model (after the accumulators are combined).
+cudaError_t apply_res(pet_plan *p, float *g, cudaStream_t st);
 }  // namespace petgb

@@ -347,10 +347,10 @@ __global__ void __launch_bounds__(kBlock) k_grad(DevPlan P, int subset, const in
           const bool count = kl_part && part == 0;
           if (!(ybar > 0.f)) {
             if (yb > 0.f) atomicOr(P.err, 1);
-            q[b] = (mode == MODE_GRAD && yb == 0.f) ? mL : 0.f;
+            q[b] = (grad_like(mode) && yb == 0.f) ? mL : 0.f;
             if (count && yb == 0.f) kl += (double)fmaxf(ybar, 0.f);
           } else {
-            if (mode == MODE_GRAD) q[b] = mL * (1.f - yb / ybar);
+            if (grad_like(mode)) q[b] = mL * (1.f - yb / ybar);
             else if (mode == MODE_EM) q[b] = mL * (yb / ybar);
             if (count) {
               const double db = ybar, dy = yb;
@@ -358,6 +358,7 @@ __global__ void __launch_bounds__(kBlock) k_grad(DevPlan P, int subset, const in
             }
           }
         }
+        if (mode == MODE_NGRAD) q[b] = -q[b];
         any |= q[b] != 0.f;
       }
     }
@@ -493,10 +494,10 @@ __device__ __forceinline__ void grad_mp_body(const DevPlan &P, int subset, int b
       const bool count = kl_out && part == 0;
       if (!(ybar > 0.f)) {
         if (yb > 0.f) atomicOr(P.err, 1);
-        q[k] = (mode == MODE_GRAD && yb == 0.f) ? mL : 0.f;
+        q[k] = (grad_like(mode) && yb == 0.f) ? mL : 0.f;
         if (count && yb == 0.f) kl += (double)fmaxf(ybar, 0.f);
       } else {
-        if (mode == MODE_GRAD) q[k] = mL * (1.f - yb / ybar);
+        if (grad_like(mode)) q[k] = mL * (1.f - yb / ybar);
         else if (mode == MODE_EM) q[k] = mL * (yb / ybar);
         if (count) {
           const double db = ybar, dy = yb;
@@ -504,6 +505,7 @@ __device__ __forceinline__ void grad_mp_body(const DevPlan &P, int subset, int b
         }
       }
     }
+    if (mode == MODE_NGRAD) q[k] = -q[k];
     any |= q[k] != 0.f;
   }
   if (mode != MODE_OBJ) {
@@ -698,10 +700,10 @@ __global__ void __launch_bounds__(kBlock) k_grad_tofw(DevPlan P, int subset, con
           const bool count = kl_part && part == 0;
           if (!(ybar > 0.f)) {
             if (yb > 0.f) atomicOr(P.err, 1);
-            qb = (mode == MODE_GRAD && yb == 0.f) ? mL : 0.f;
+            qb = (grad_like(mode) && yb == 0.f) ? mL : 0.f;
             if (count && yb == 0.f) kl += (double)fmaxf(ybar, 0.f);
           } else {
-            if (mode == MODE_GRAD) qb = mL * (1.f - yb / ybar);
+            if (grad_like(mode)) qb = mL * (1.f - yb / ybar);
             else if (mode == MODE_EM) qb = mL * (yb / ybar);
             if (count) {
               const double db = ybar, dy = yb;
@@ -709,6 +711,7 @@ __global__ void __launch_bounds__(kBlock) k_grad_tofw(DevPlan P, int subset, con
             }
           }
         }
+        if (mode == MODE_NGRAD) qb = -qb;
         any |= qb != 0.f;
       }
       if (b < T) s_acc[b * kBlock + threadIdx.x] = qb;

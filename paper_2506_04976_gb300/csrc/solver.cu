@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "pet_internal.cuh"
@@ -49,6 +50,9 @@ struct UpdArgs {
   double *tau_log;   // indexed by k (may be NULL)
   const int *subset_dev;     // if set, the subset is read from device memory (batches)
   const long long *k_dev;    // if set, the iteration index is read from device memory
+  const float *w_dev;        // SVRG: weight 1/p_i of the sampled subset (NULL: n)
+  const float *gSh;          // SVRG with non-uniform weights: beta grad S(xhat) (else NULL)
+  int *sub_log;              // indexed by k: subset used, -1 at SVRG refreshes (may be NULL)
 };
 
 __device__ __forceinline__ float step_of(const UpdArgs &a, long long ki) {
@@ -81,7 +85,7 @@ template <int ALGO>
 __device__ __forceinline__ void upd_body(const UpdArgs &a, int bx, int by, int z) {
   __shared__ float tin[32][33];
   __shared__ float tout[32][33];
-  __shared__ float s_tau;
+  __shared__ float s_tau, s_w;
   __shared__ int s_sub;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int x0 = bx * 32, y0 = by * 32;
@@ -90,7 +94,11 @@ __device__ __forceinline__ void upd_body(const UpdArgs &a, int bx, int by, int z
     const long long k = a.k_dev ? *a.k_dev : a.k;
     s_tau = step_of(a, k);
     s_sub = a.subset_dev ? *a.subset_dev : a.subset;
-    if (bx == 0 && by == 0 && z == 0 && a.tau_log) a.tau_log[k] = s_tau;
+    s_w = a.w_dev ? *a.w_dev : (float)a.n;
+    if (bx == 0 && by == 0 && z == 0) {
+      if (a.tau_log) a.tau_log[k] = s_tau;
+      if (a.sub_log) a.sub_log[k] = ALGO == 3 ? -1 : s_sub;
+    }
   }
   if (ALGO != 3) {
     for (int j = ty; j < 32; j += 8) {
@@ -123,7 +131,12 @@ __device__ __forceinline__ void upd_body(const UpdArgs &a, int bx, int by, int z
           a.G[i] = Gi + (gf - ti);
           Ti[i] = gf;
         } else {
-          dir = fmaf(nf, gi - Ti[i], a.G[i]) + a.gS[i];
+          // SVRG, eq. 9: w (grad D_i(x) - grad D_i(xhat)) + grad D(xhat) + beta grad S(x), the
+          // prior part telescoped for w = n; a table-free solver's g already holds the
+          // difference.  For w != n the prior part is (w/n)(gS - gSh) + gSh exactly.
+          const float w = s_w;
+          dir = fmaf(w, Ti ? gi - Ti[i] : gi, a.G[i]) + a.gS[i];
+          if (a.gSh) dir = fmaf(w / nf - 1.f, a.gS[i] - a.gSh[i], dir);
         }
       }
       xn = fmaf(-tau * a.D[i], dir, a.x[i]);
@@ -283,6 +296,68 @@ __global__ void k_bb_final(const double *part, int nb, SolverState *st) {
   st->have_snapshot = 1;
 }
 
+// Importance sampling at an SVRG refresh (Sec. 2.4): FP64 partial sums of
+// ||g_t + gS/n||^2 for subset t = blockIdx.y, over a grid-stride share of the image.
+// src is the table entry of t (table == true) or an image-sized accumulator holding
+// grad D_t (table == false), which is then added into G and cleared.
+__global__ void k_sub_norms(float *__restrict__ src, const float *__restrict__ gS, float *__restrict__ G,
+                            int n, size_t N, int from_table, double *__restrict__ part) {
+  const int t = blockIdx.y;
+  float *g = from_table ? src + (size_t)t * N : src;
+  double acc = 0.0;
+  const float inv_n = 1.f / (float)n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    const float v = g[i];
+    const double f = (double)fmaf(gS[i], inv_n, v);
+    acc += f * f;
+    if (!from_table) {
+      G[i] += v;
+      g[i] = 0.f;
+    }
+  }
+  const double b = warp_block_sum(acc);
+  if (threadIdx.x == 0) part[(size_t)t * gridDim.x + blockIdx.x] = b;
+}
+
+// p_t = ||grad f_t|| / sum_j ||grad f_j|| from the partial sums (uniform if all vanish).
+__global__ void k_probs(const double *__restrict__ part, int nb, int n, double *__restrict__ prob) {
+  __shared__ double nrm[1024];
+  for (int t = 0; t < n; ++t) {
+    double sacc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) sacc += part[(size_t)t * nb + b];
+    sacc = warp_block_sum(sacc);
+    if (threadIdx.x == 0) nrm[t] = sqrt(sacc);
+  }
+  if (threadIdx.x != 0) return;
+  double tot = 0.0;
+  for (int t = 0; t < n; ++t) tot += nrm[t];
+  for (int t = 0; t < n; ++t) prob[t] = tot > 0.0 ? nrm[t] / tot : 1.0 / n;
+}
+
+// Importance draw of iteration k: u = (z >> 11) 2^-53 with z the k-th output of the
+// splitmix64 stream from `seed`; the subset is the smallest t with u below the FP64
+// cumulative sum of p (the last t with p_t > 0 if rounding leaves u above the sum).
+__global__ void k_draw(const double *__restrict__ prob, int n, unsigned long long seed, long long k,
+                       int *__restrict__ sub, float *__restrict__ w) {
+  if (threadIdx.x != 0) return;
+  unsigned long long z = seed + (unsigned long long)(k + 1) * 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  z = z ^ (z >> 31);
+  const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  double c = 0.0;
+  int pick = -1, last = 0;
+  for (int t = 0; t < n; ++t) {
+    const double pt = prob[t];
+    if (pt > 0.0) last = t;
+    c += pt;
+    if (pick < 0 && pt > 0.0 && u < c) pick = t;
+  }
+  if (pick < 0) pick = last;
+  *sub = pick;
+  *w = (float)(1.0 / prob[pick]);
+}
+
 unsigned grid_elems(size_t N) { return (unsigned)std::min<size_t>((size_t)152 * 8, (N + 255) / 256); }
 
 uint64_t splitmix64(uint64_t &s) {
@@ -291,6 +366,43 @@ uint64_t splitmix64(uint64_t &s) {
   z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
   return z ^ (z >> 31);
 }
+
+// Herman-Meyer order (Sec. 2.4): with the prime factors p1 <= p2 <= ... of n, epoch
+// position j, written in mixed radix with its lowest digit in base p1, visits the subset
+// whose digits are weighted n/p1, n/(p1 p2), ... (bit reversal when n is a power of 2).
+std::vector<int> herman_meyer(int n) {
+  std::vector<int> f;
+  int r = n;
+  for (int q = 2; q <= r; ++q)
+    while (r % q == 0) { f.push_back(q); r /= q; }
+  std::vector<int> out(n);
+  for (int j = 0; j < n; ++j) {
+    int rest = j, w = n, idx = 0;
+    for (int p : f) {
+      w /= p;
+      idx += (rest % p) * w;
+      rest /= p;
+    }
+    out[j] = idx;
+  }
+  return out;
+}
+
+// Cofactor order (Sec. 2.4): generators g of Z_n (gcd(g, n) = 1), nearest to 0.3 n or
+// 0.7 n first (distance compared as min(|10 g - 3 n|, |10 g - 7 n|), ties to the smaller g).
+std::vector<int> cofactor_generators(int n) {
+  std::vector<int> g;
+  for (int c = 1; c < n; ++c) {
+    int a = c, b = n;
+    while (b) { const int t = a % b; a = b; b = t; }
+    if (a == 1) g.push_back(c);
+  }
+  auto dist = [n](int c) { return std::min(std::abs(10 * c - 3 * n), std::abs(10 * c - 7 * n)); };
+  std::stable_sort(g.begin(), g.end(), [&](int a, int b) { return dist(a) < dist(b); });
+  return g;
+}
+
+constexpr int kNormBlocks = 64;
 
 }  // namespace
 
@@ -310,9 +422,25 @@ struct pet_solver {
   int npart = 0;
   SolverState *st = nullptr;
   double *tau_log = nullptr;
+  int *sub_log = nullptr;   // subset of every iteration, -1 at SVRG refreshes
   long long tau_cap = 0;
+  // sampling rules of Sec. 2.4
+  std::vector<int> hm;      // Herman-Meyer order
+  std::vector<int> gens;    // cofactor generators, ranked
+  // importance sampling (SVRG): probabilities, their partial sums, the drawn subset and
+  // its weight, and beta grad S at the snapshot
+  double *prob = nullptr, *norm_part = nullptr;
+  int *d_sub = nullptr;
+  float *d_w = nullptr, *gSh = nullptr;
+  // table-free SVRG: the snapshot in the transposed layout (xhat_old holds the canonical one)
+  float *xhatT = nullptr;
   bool initialised = false;
   cudaStream_t cap_stream = nullptr;
+  // The prior's gradient depends only on x, so each iteration computes it on a second
+  // stream, forked after the previous update and joined before the next one; its blocks
+  // fill the SMs that the subset-gradient launch leaves idle in its last wave.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t exec[2] = {nullptr, nullptr};  // [0] plain epoch, [1] epoch starting with a refresh
   // optional event timing of the fused subset-gradient kernel: one (start, stop) pair per
   // launch slot of an SVRG outer loop (or of an epoch for SGD/SAGA)
@@ -329,13 +457,19 @@ static pet_status grow_tau_log(pet_solver *s, long long need) {
   if (need <= s->tau_cap) return PET_OK;
   long long cap = std::max(need, 2 * s->tau_cap + 1024);
   double *nl = nullptr;
+  int *ns = nullptr;
   if (cudaMalloc(&nl, cap * sizeof(double)) != cudaSuccess) return PET_ERR_NOMEM;
+  if (cudaMalloc(&ns, cap * sizeof(int)) != cudaSuccess) { cudaFree(nl); return PET_ERR_NOMEM; }
   cudaMemset(nl, 0, cap * sizeof(double));
+  cudaMemset(ns, 0xff, cap * sizeof(int));
   if (s->tau_log) {
     cudaMemcpy(nl, s->tau_log, s->tau_cap * sizeof(double), cudaMemcpyDeviceToDevice);
+    cudaMemcpy(ns, s->sub_log, s->tau_cap * sizeof(int), cudaMemcpyDeviceToDevice);
     cudaFree(s->tau_log);
+    cudaFree(s->sub_log);
   }
   s->tau_log = nl;
+  s->sub_log = ns;
   s->tau_cap = cap;
   for (auto &e : s->exec)
     if (e) { cudaGraphExecDestroy(e); e = nullptr; }
@@ -347,9 +481,14 @@ static void solver_free(pet_solver *s) {
   for (auto &e : s->exec)
     if (e) cudaGraphExecDestroy(e);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  if (s->side) cudaStreamDestroy(s->side);
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->ev_join) cudaEventDestroy(s->ev_join);
   for (auto e : s->ev0) cudaEventDestroy(e);
   for (auto e : s->ev1) cudaEventDestroy(e);
   cudaFree(s->x); cudaFree(s->D); cudaFree(s->g); cudaFree(s->gS); cudaFree(s->H);
+  cudaFree(s->sub_log); cudaFree(s->prob); cudaFree(s->norm_part); cudaFree(s->d_sub); cudaFree(s->d_w);
+  cudaFree(s->gSh); cudaFree(s->xhatT);
   cudaFree(s->table); cudaFree(s->G); cudaFree(s->xhat_old); cudaFree(s->Gfull_old);
   cudaFree(s->part); cudaFree(s->st); cudaFree(s->tau_log);
   delete s;
@@ -362,8 +501,11 @@ extern "C" pet_status pet_solver_create(pet_plan *plan, const pet_solver_opts *o
   const pet_solver_opts &o = *opts;
   if (o.algo < 0 || o.algo > 2 || o.step_rule < 0 || o.step_rule > 4 || o.precond_kind < 0 ||
       o.precond_kind > 1 || (o.algo == PET_SVRG && o.omega < 1) || (o.n_pc > 0 && !o.pc_iters) ||
-      (o.norder > 0 && !o.order))
+      (o.norder > 0 && !o.order) || o.sampling < PET_SAMPLE_PERM || o.sampling > PET_SAMPLE_IMPORTANCE ||
+      ((o.sampling == PET_SAMPLE_IMPORTANCE || o.low_memory) && o.algo != PET_SVRG))
     return PET_ERR_ARG;
+  if ((o.sampling == PET_SAMPLE_IMPORTANCE || o.low_memory) && o.deterministic) return PET_ERR_UNSUPPORTED;
+  if (o.sampling == PET_SAMPLE_IMPORTANCE && plan->g.nsubsets > 1024) return PET_ERR_UNSUPPORTED;
   pet_solver *s = new pet_solver();
   s->plan = plan;
   s->o = o;
@@ -384,11 +526,23 @@ extern "C" pet_status pet_solver_create(pet_plan *plan, const pet_solver_opts *o
             cudaMalloc(&s->part, s->npart * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&s->st, sizeof(SolverState)) == cudaSuccess;
   if (ok && o.algo != PET_SGD)
-    ok = cudaMalloc(&s->table, N * 4 * (size_t)s->n) == cudaSuccess && cudaMalloc(&s->G, N * 4) == cudaSuccess;
+    ok = (o.low_memory || cudaMalloc(&s->table, N * 4 * (size_t)s->n) == cudaSuccess) &&
+         cudaMalloc(&s->G, N * 4) == cudaSuccess;
   if (ok && o.algo == PET_SVRG)
     ok = cudaMalloc(&s->xhat_old, N * 4) == cudaSuccess && cudaMalloc(&s->Gfull_old, N * 4) == cudaSuccess;
+  if (ok && o.low_memory) ok = cudaMalloc(&s->xhatT, N * 4) == cudaSuccess;
+  if (ok && o.sampling == PET_SAMPLE_IMPORTANCE)
+    ok = cudaMalloc(&s->prob, s->n * sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&s->norm_part, (size_t)s->n * kNormBlocks * sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&s->d_sub, sizeof(int)) == cudaSuccess && cudaMalloc(&s->d_w, sizeof(float)) == cudaSuccess &&
+         cudaMalloc(&s->gSh, N * 4) == cudaSuccess;
+  if (ok && o.sampling == PET_SAMPLE_HM) s->hm = herman_meyer(s->n);
+  if (ok && o.sampling == PET_SAMPLE_COFACTOR) s->gens = cofactor_generators(s->n);
   if (!ok) { solver_free(s); return PET_ERR_NOMEM; }
-  if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     solver_free(s);
     return PET_ERR_CUDA;
   }
@@ -417,6 +571,14 @@ extern "C" pet_status pet_solver_set_image(pet_solver *s, const float *x, void *
   return PET_OK;
 }
 
+extern "C" long long pet_solver_subsets(const pet_solver *s, int *subsets, long long cap) {
+  if (!s || !subsets) return 0;
+  const long long n = std::min(cap, s->k);
+  if (n > 0 && s->sub_log && cudaMemcpy(subsets, s->sub_log, n * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return 0;
+  return n;
+}
+
 extern "C" long long pet_solver_taus(const pet_solver *s, double *taus, long long cap) {
   if (!s || !taus) return 0;
   const long long n = std::min(cap, s->k);
@@ -428,6 +590,20 @@ extern "C" long long pet_solver_taus(const pet_solver *s, double *taus, long lon
 static int subset_of(pet_solver *s, long long k) {
   if (!s->order.empty()) return k < (long long)s->order.size() ? s->order[k] : -1;
   const int n = s->n;
+  switch (s->o.sampling) {
+    case PET_SAMPLE_REPLACE: {  // output k of the splitmix64 stream from the seed
+      uint64_t st = s->o.seed + (uint64_t)k * 0x9e3779b97f4a7c15ULL;
+      return (int)(((splitmix64(st) >> 32) * (uint64_t)n) >> 32);
+    }
+    case PET_SAMPLE_HM: return s->hm[k % n];
+    case PET_SAMPLE_COFACTOR: {
+      if (s->gens.empty()) return 0;
+      const long long g = s->gens[(k / n) % (long long)s->gens.size()];
+      return (int)(((k % n) * g) % n);
+    }
+    case PET_SAMPLE_IMPORTANCE: return 0;  // drawn on the device
+    default: break;
+  }
   if (k % n == 0 || s->perm.empty()) {
     s->perm.resize(n);
     for (int i = 0; i < n; ++i) s->perm[i] = i;
@@ -466,16 +642,24 @@ static cudaError_t record(pet_solver *s, cudaEvent_t ev, cudaStream_t st) {
 }
 
 // Data gradient of subset `sub` at x into `dst` (zeroed by the caller unless deterministic).
+// sub_dev (may be NULL) supplies the subset from device memory; img/imgT (default: the
+// iterate in both layouts) and mode (MODE_NGRAD subtracts) serve the table-free SVRG.
 static pet_status data_grad(pet_solver *s, int sub, float *dst, cudaStream_t st, int slot = -1,
-                            bool combine = true) {
+                            bool combine = true, const int *sub_dev = nullptr, const float *img = nullptr,
+                            const float *imgT = nullptr, int mode = MODE_GRAD) {
   pet_plan *p = s->plan;
   if (s->o.deterministic) {
     pet_status e = pet_objective_grad(p, sub, s->x, dst, nullptr, nullptr, PET_GRAD_DETERMINISTIC, st);
     return e;
   }
+  const float *im = img ? img : s->x, *imT = imgT ? imgT : p->d_xT;
+  if (p->res) {  // the projector reads G x (both layouts rebuilt from the canonical image)
+    SCK(prepare_image(p, im, &im, st));
+    imT = p->d_xT;
+  }
   const bool prof = s->profile && slot >= 0 && slot < (int)s->ev0.size();
   if (prof) SCK(record(s, s->ev0[slot], st));
-  SCK(launch_grad(p->dp, sub, nullptr, s->x, p->d_xT, dst, p->d_gT, nullptr, MODE_GRAD, nullptr, st));
+  SCK(launch_grad(p->dp, sub, sub_dev, im, imT, dst, p->d_gT, nullptr, mode, nullptr, st));
   if (prof) {
     SCK(record(s, s->ev1[slot], st));
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -487,6 +671,7 @@ static pet_status data_grad(pet_solver *s, int sub, float *dst, cudaStream_t st,
     SCK(launch_transpose(p->d_gT, dst, p->g.nx, p->g.ny, p->g.nz, 1, 1, st));  // add
     note_launch();
     k_clear2<<<grid_elems(s->N / 4), 256, 0, st>>>(p->d_gT, nullptr, s->N);
+    SCK(apply_res(p, dst, st));
   }
   return PET_OK;
 }
@@ -497,6 +682,21 @@ static RdpArgs prior_args(const pet_solver *s, float scale) {
   rp.dx = s->plan->g.dx; rp.dy = s->plan->g.dy; rp.dz = s->plan->g.dz;
   rp.gamma = s->o.gamma; rp.eps = s->o.eps; rp.scale = scale; rp.kappa = s->o.kappa;
   return make_rdp_args(rp);
+}
+
+// grad S(x) into gS on the side stream, ordered after everything enqueued on st so far;
+// join_prior makes st wait for it.  Under stream capture the two become graph branches.
+static pet_status fork_prior(pet_solver *s, cudaStream_t st) {
+  SCK(cudaEventRecord(s->ev_fork, st));
+  SCK(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
+  SCK(launch_rdp(prior_args(s, s->o.beta), s->x, s->gS, nullptr, nullptr, 0, nullptr, s->side));
+  SCK(cudaEventRecord(s->ev_join, s->side));
+  return PET_OK;
+}
+
+static pet_status join_prior(pet_solver *s, cudaStream_t st) {
+  SCK(cudaStreamWaitEvent(st, s->ev_join, 0));
+  return PET_OK;
 }
 
 static pet_status precond_update(pet_solver *s, cudaStream_t st) {
@@ -518,8 +718,11 @@ static UpdArgs upd_args(pet_solver *s, int sub, long long k) {
   a.N = s->N; a.n = s->n; a.subset = sub < 0 ? 0 : sub; a.k = k;
   a.rule = s->o.step_rule; a.tau0 = (float)s->o.tau0; a.eta = (float)s->o.eta;
   a.st = s->st; a.tau_log = s->tau_log;
-  a.subset_dev = nullptr;
+  a.subset_dev = s->d_sub;
   a.k_dev = nullptr;
+  a.w_dev = s->d_w;
+  a.gSh = s->gSh;
+  a.sub_log = s->sub_log;
   return a;
 }
 
@@ -557,16 +760,54 @@ static pet_status iterate(pet_solver *s, long long k, int sub, cudaStream_t st) 
   const bool refresh = s->o.algo == PET_SVRG && k % ((long long)s->o.omega * s->n) == 0;
   // the transposed copy of x is kept current by the update kernel
   (void)p;
+  if (!refresh && sub < 0) return PET_ERR_ARG;
+  pet_status e = fork_prior(s, st);
+  if (e != PET_OK) return e;
+  const bool importance = s->o.sampling == PET_SAMPLE_IMPORTANCE;
   if (refresh) {
-    for (int t = 0; t < s->n; ++t) {
-      float *Tt = s->table + (size_t)t * s->N;
-      if (!s->o.deterministic) SCK(cudaMemsetAsync(Tt, 0, s->N * 4, st));
-      pet_status e = data_grad(s, t, Tt, st, slot_of(s, k, t));
+    if (!s->o.low_memory) {
+      for (int t = 0; t < s->n; ++t) {
+        float *Tt = s->table + (size_t)t * s->N;
+        if (!s->o.deterministic) SCK(cudaMemsetAsync(Tt, 0, s->N * 4, st));
+        e = data_grad(s, t, Tt, st, slot_of(s, k, t));
+        if (e != PET_OK) return e;
+      }
+      note_launch();
+      k_sum_table<<<ge, 256, 0, st>>>(s->table, s->G, nullptr, s->n, s->N);
+      e = join_prior(s, st);
       if (e != PET_OK) return e;
+      if (importance) {
+        note_launch();
+        k_sub_norms<<<dim3(kNormBlocks, s->n), 256, 0, st>>>(s->table, s->gS, nullptr, s->n, s->N, 1,
+                                                             s->norm_part);
+      }
+    } else if (!importance) {
+      // table-free: the full data gradient at the snapshot in one launch over all views
+      SCK(cudaMemsetAsync(s->G, 0, s->N * 4, st));
+      e = data_grad(s, -1, s->G, st, slot_of(s, k, 0));
+      if (e != PET_OK) return e;
+      e = join_prior(s, st);
+      if (e != PET_OK) return e;
+    } else {
+      // table-free with importance sampling: each subset gradient is folded into G
+      // (and cleared) by the kernel that takes its norm
+      SCK(cudaMemsetAsync(s->G, 0, s->N * 4, st));
+      e = join_prior(s, st);
+      if (e != PET_OK) return e;
+      for (int t = 0; t < s->n; ++t) {
+        e = data_grad(s, t, s->g, st, slot_of(s, k, t));
+        if (e != PET_OK) return e;
+        note_launch();
+        k_sub_norms<<<dim3(kNormBlocks, 1), 256, 0, st>>>(s->g, s->gS, s->G, s->n, s->N, 0,
+                                                          s->norm_part + (size_t)t * kNormBlocks);
+      }
     }
-    note_launch();
-    k_sum_table<<<ge, 256, 0, st>>>(s->table, s->G, nullptr, s->n, s->N);
-    SCK(launch_rdp(prior_args(s, s->o.beta), s->x, s->gS, nullptr, nullptr, 0, nullptr, st));
+    if (importance) {
+      note_launch();
+      k_probs<<<1, 256, 0, st>>>(s->norm_part, kNormBlocks, s->n, s->prob);
+      SCK(cudaMemcpyAsync(s->gSh, s->gS, s->N * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    if (s->xhatT) SCK(cudaMemcpyAsync(s->xhatT, p->d_xT, s->N * 4, cudaMemcpyDeviceToDevice, st));
     note_launch();
     k_bb_dots<<<ge, 256, 0, st>>>(s->x, s->xhat_old, s->G, s->gS, s->Gfull_old, s->N, s->part);
     note_launch();
@@ -574,10 +815,24 @@ static pet_status iterate(pet_solver *s, long long k, int sub, cudaStream_t st) 
     note_launch();
     k_update<3><<<tile_grid(s), dim3(32, 8), 0, st>>>(upd_args(s, -1, k));
   } else {
-    if (sub < 0) return PET_ERR_ARG;
-    pet_status e = data_grad(s, sub, s->g, st, slot_of(s, k, -1), false);
+    const int *sub_dev = nullptr;
+    if (importance) {
+      note_launch();
+      k_draw<<<1, 32, 0, st>>>(s->prob, s->n, (unsigned long long)s->o.seed, k, s->d_sub, s->d_w);
+      sub_dev = s->d_sub;
+    }
+    e = data_grad(s, sub, s->g, st, slot_of(s, k, -1), false, sub_dev);
     if (e != PET_OK) return e;
-    SCK(launch_rdp(prior_args(s, s->o.beta), s->x, s->gS, nullptr, nullptr, 0, nullptr, st));
+    if (s->o.low_memory) {  // minus the subset gradient at the snapshot
+      e = data_grad(s, sub, s->g, st, -1, false, sub_dev, s->xhat_old, s->xhatT, MODE_NGRAD);
+      if (e != PET_OK) return e;
+    }
+    if (p->res) {  // (P G)^T = G P^T, applied once to the combined accumulators
+      SCK(from_frames(p, s->g, st));
+      SCK(apply_res(p, s->g, st));
+    }
+    e = join_prior(s, st);
+    if (e != PET_OK) return e;
     const UpdArgs a = upd_args(s, sub, k);
     note_launch();
     if (s->o.algo == PET_SGD) k_update<0><<<tile_grid(s), dim3(32, 8), 0, st>>>(a);
@@ -720,12 +975,17 @@ struct pet_batch {
   int buf = 0;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cap = nullptr;
+  cudaStream_t side = nullptr;  // the prior's gradients, concurrent with the subset gradients
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 static void batch_free(pet_batch *b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
   for (int i = 0; i < 2; ++i) {
     if (b->up[i]) cudaEventDestroy(b->up[i]);
     cudaFreeHost(b->h_sub[i]);
@@ -749,6 +1009,7 @@ extern "C" pet_status pet_batch_create(pet_solver *const *solvers, int n, int it
     if (si->plan->T != 1 || si->o.kappa) return PET_ERR_UNSUPPORTED;
     for (int j = 0; j < i; ++j)
       if (solvers[j]->plan == si->plan || solvers[j] == si) return PET_ERR_ARG;  // scratch is per plan
+    if (si->plan->res) return PET_ERR_UNSUPPORTED;  // batched launches read x directly
   }
   pet_batch *b = new pet_batch();
   b->s.assign(solvers, solvers + n);
@@ -771,6 +1032,9 @@ extern "C" pet_status pet_batch_create(pet_solver *const *solvers, int n, int it
          cudaMallocHost(&b->h_k[i], ne * sizeof(long long)) == cudaSuccess &&
          cudaEventCreateWithFlags(&b->up[i], cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+       cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) == cudaSuccess &&
        cudaMemset(b->d_sub, 0, ne * sizeof(int)) == cudaSuccess &&
        cudaMemset(b->d_k, 0, ne * sizeof(long long)) == cudaSuccess;
   if (!ok) { batch_free(b); return PET_ERR_NOMEM; }
@@ -834,8 +1098,12 @@ static pet_status batch_tables(pet_batch *b) {
 // One batch iteration j of the captured epoch (all instances).
 static pet_status batch_iteration(pet_batch *b, int j, cudaStream_t st) {
   const int n = b->nj;
+  SCK(cudaEventRecord(b->ev_fork, st));
+  SCK(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
+  SCK(launch_rdp_batch(b->d_rjobs, b->d_rbegin, n, b->rblocks, b->side));
+  SCK(cudaEventRecord(b->ev_join, b->side));
   SCK(launch_grad_batch(b->d_gjobs + (size_t)j * n, b->d_gbegin, n, b->gblocks, b->K, b->split, st));
-  SCK(launch_rdp_batch(b->d_rjobs, b->d_rbegin, n, b->rblocks, st));
+  SCK(cudaStreamWaitEvent(st, b->ev_join, 0));
   note_launch();
   if (b->algo == PET_SAGA)
     k_update_batch<1><<<b->ublocks, dim3(32, 8), 0, st>>>(b->d_ujobs + (size_t)j * n, b->d_ubegin, n);

@@ -1,0 +1,143 @@
+"""Subset sampling rules (Sec. 2.4) and the table-free SVRG (Sec. 2.1) of the CUDA
+solver against the FP64 oracle: the subsets the solver used equal the oracle's order
+exactly (integer work), and the trajectories agree within the solver tolerance of
+1e-4 relative L2 after three epochs.
+
+Importance sampling draws on the device from probabilities computed in FP32/FP64 on
+the GPU and in FP64 by the oracle; the draw compares a 53-bit uniform with cumulative
+sums that differ by ~1e-7 relative, so a different draw would need u within ~1e-7 of a
+boundary (probability ~1e-5 over the draws of this test)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2506_04976_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+_P = {}
+
+
+def problem(key):
+    if key not in _P:
+        if key == "c1":
+            p = synth.make_problem("c1", 3)
+        elif key == "3d":
+            p = synth.make_problem("c2", 3, nx=32, nz=13, nrad=56, nview=24, nsub=6)
+        else:
+            p = synth.make_problem("c3", 3, nx=28, nz=9, nrad=48, nview=20, nsub=4)
+        from paper_2506_04976_gb300 import binding as pet
+        g = p["geom"]
+        plan = pet.Plan(g, p["nsub"])
+        mu32, sens32 = p["mu"].astype(np.float32), p["sens"].astype(np.float32)
+        plan.set_data(torch.from_numpy(p["y"].astype(np.int32)).to(DEV), torch.from_numpy(p["r"]).to(DEV),
+                      torch.from_numpy(mu32).to(DEV), torch.from_numpy(sens32).to(DEV))
+        G = O.Geometry(g)
+        m = O.multiplicative(G, mu32, sens32)
+        sens = O.sensitivity(G, 1, -1, m)
+        x0 = np.full(G.img_shape, float(p["x_true"].mean()), np.float32)
+        _P[key] = (p, plan, G, m, sens, x0)
+    return _P[key]
+
+
+def _kw(p, n):
+    return dict(omega=2, step_rule=O.STEP_VANISH, tau0=1.0, eta=0.02, precond_kind=1, alpha=1.0,
+                delta_rel=1e-6, pc_iters=(0, n, 2 * n), beta=p["beta"], gamma=p["gamma"], eps=p["eps"])
+
+
+def _gpu(key, algo, niter, seed, sampling, low_memory=False, use_graph=True, order=None):
+    from paper_2506_04976_gb300 import binding as pet
+    p, plan, G, m, sens, x0 = problem(key)
+    s = pet.Solver(plan, algo=algo, seed=seed, sampling=sampling, low_memory=low_memory, use_graph=use_graph,
+                   order=order, **_kw(p, p["nsub"]))
+    s.set_image(torch.from_numpy(x0).to(DEV))
+    s.run(niter)
+    torch.cuda.synchronize()
+    return s.image().cpu().numpy().astype(np.float64), s.subsets(), s
+
+
+def _oracle(key, algo, niter, order, sampling=O.SAMPLE_PERM, seed=0):
+    p, plan, G, m, sens, x0 = problem(key)
+    subs = np.zeros(niter, np.int32)
+    xo, _, _ = O.solve(G, x0, m, p["r"], p["y"], sens, algo=algo, nsub=p["nsub"], niter=niter, order=order,
+                       sampling=sampling, sample_seed=seed, subsets_out=subs, **_kw(p, p["nsub"]))
+    return xo, subs
+
+
+@pytest.mark.parametrize("rule", [O.SAMPLE_PERM, O.SAMPLE_REPLACE, O.SAMPLE_HM, O.SAMPLE_COFACTOR])
+@pytest.mark.parametrize("algo", [O.SVRG, O.SAGA, O.SGD])
+def test_sampling_rule_matches_oracle(rule, algo):
+    key = "3d"
+    p = problem(key)[0]
+    n = p["nsub"]
+    niter = 3 * n + 1
+    seed = 2024
+    order = O.subset_order(seed, n, niter, rule)
+    xg, sg, _ = _gpu(key, algo, niter, seed, rule)
+    xo, so = _oracle(key, algo, niter, order)
+    assert np.array_equal(sg, so), (sg, so)
+    rel = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    assert rel <= 1e-4, rel
+
+
+@pytest.mark.parametrize("key", ["c1", "3d", "tof"])
+def test_importance_sampling_svrg_matches_oracle(key):
+    p = problem(key)[0]
+    n = p["nsub"]
+    niter = 3 * n + 1
+    seed = 77
+    xg, sg, _ = _gpu(key, O.SVRG, niter, seed, O.SAMPLE_IMPORTANCE)
+    xo, so = _oracle(key, O.SVRG, niter, np.zeros(niter, np.int32), O.SAMPLE_IMPORTANCE, seed)
+    assert np.array_equal(sg, so), (sg, so)
+    assert (sg[::2 * n] == -1).all()
+    rel = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    assert rel <= 1e-4, rel
+
+
+@pytest.mark.parametrize("key", ["c1", "3d", "tof"])
+@pytest.mark.parametrize("sampling", [O.SAMPLE_PERM, O.SAMPLE_IMPORTANCE])
+def test_table_free_svrg_matches_oracle(key, sampling):
+    """The table-free SVRG recomputes grad D_i(xhat) every inner iteration; its
+    iterates are those of the tabled method (the oracle keeps the table)."""
+    p = problem(key)[0]
+    n = p["nsub"]
+    niter = 3 * n + 1
+    seed = 5
+    order = O.subset_order(seed, n, niter) if sampling == O.SAMPLE_PERM else np.zeros(niter, np.int32)
+    xg, sg, _ = _gpu(key, O.SVRG, niter, seed, sampling, low_memory=True)
+    xo, so = _oracle(key, O.SVRG, niter, order, sampling, seed)
+    assert np.array_equal(sg, so)
+    rel = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    assert rel <= 1e-4, rel
+
+
+def test_graph_and_plain_agree_for_device_draws():
+    key = "3d"
+    n = problem(key)[0]["nsub"]
+    a, sa, _ = _gpu(key, O.SVRG, 3 * n, 11, O.SAMPLE_IMPORTANCE, use_graph=True)
+    b, sb, _ = _gpu(key, O.SVRG, 3 * n, 11, O.SAMPLE_IMPORTANCE, use_graph=False)
+    assert np.array_equal(sa, sb)
+    assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(a)
+
+
+def test_explicit_order_overrides_host_rules():
+    key = "c1"
+    n = problem(key)[0]["nsub"]
+    order = O.subset_order(3, n, 2 * n, O.SAMPLE_HM)[::-1].copy()
+    _, sg, _ = _gpu(key, O.SAGA, 2 * n, 0, O.SAMPLE_REPLACE, order=order)
+    assert np.array_equal(sg, order)
+
+
+def test_invalid_combinations_rejected():
+    from paper_2506_04976_gb300 import binding as pet
+    p, plan = problem("c1")[:2]
+    for kw in (dict(algo=pet.SAGA, sampling=pet.SAMPLE_IMPORTANCE), dict(algo=pet.SGD, low_memory=True),
+               dict(algo=pet.SVRG, sampling=9)):
+        with pytest.raises(pet.PetError) as e:
+            pet.Solver(plan, **kw)
+        assert e.value.status == 1
+    with pytest.raises(pet.PetError) as e:
+        pet.Solver(plan, algo=pet.SVRG, low_memory=True, deterministic=True)
+    assert e.value.status == 6
