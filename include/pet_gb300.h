@@ -112,9 +112,9 @@ const float *pet_plan_sensitivity(const pet_plan *plan, int subset);
 
 /* Launch shape of the fused subset-gradient kernel: planes per thread (1, 2 or 4; more
  * than 1 only without TOF: those LORs of one view and radial bin share their in-plane
- * sample positions) and parts per LOR (1, 2 or 4: interleaved plane sets of one LOR
- * processed by different warps).  0 selects the built-in heuristic.  Results are the
- * same up to FP32 summation order. */
+ * sample positions) and parts per LOR (1, 2, 4, or 8 without TOF: interleaved sets of
+ * the driving planes of one LOR processed by different warps).  0 selects the built-in
+ * heuristic.  Results are the same up to FP32 summation order. */
 pet_status pet_plan_set_grad_shape(pet_plan *plan, int planes_per_thread, int parts);
 
 /* Autotuner: times every valid launch shape on subset 0 of the bound data (a uniform

@@ -45,7 +45,6 @@ struct DevPlan {
   int *err;             // device error word (bit 0: infeasible ybar)
   float tof_inv_w;       // 1 / bin width
   float tof_reach;       // 3 sigma / bin width
-  int tof_wmax;          // edges examined per sample: ceil(6 sigma / w) + 3
   const float *erfc_tab; // erfc(j amax / kErfcTab), j = 0..kErfcTab (TOF)
   float erfc_scale;      // kErfcTab / amax
   int grad_k;           // fused gradient: planes per thread (non-TOF; 0 = heuristic)

@@ -124,14 +124,17 @@ __device__ __forceinline__ void back_lor(const DevPlan &P, const Lor &L, float *
 
 // TOF with a window of bin edges: the per-thread bin accumulators live in shared
 // memory (column threadIdx.x of [TT][kBlock] arrays) so that a sample touches only the
-// edges within 3 sigma of it.  Edges klo = floor((t - 3 sigma - e0)/w) - 1 ... klo + wmax
-// cover that reach with one edge of margin on each side; every bin outside has both
-// edges clamped on the same side and weight exactly zero.  Samples whose interpolated
-// value is exactly zero contribute nothing and skip the TOF work.
+// bins that meet [t - 3 sigma, t + 3 sigma]: with kt = (t - e0)/w, bins
+// floor(kt - reach - m) ... floor(kt + reach + m), reach = 3 sigma / w, i.e. edges klo ..
+// khi.  The margin m = 1/64 bin (0.5 mm at 31 mm bins) exceeds the FP32 error of kt by
+// four orders of magnitude, so every bin left out has both edges clamped on the same
+// side and weight exactly zero.  Samples whose interpolated value is exactly zero
+// contribute nothing and skip the TOF work.
 __device__ __forceinline__ void tof_window(const DevPlan &P, float t, int T, int &klo, int &khi) {
-  const float kf = (t - P.tof_e0) * P.tof_inv_w - P.tof_reach;
-  klo = max(0, (int)floorf(fmaxf(kf, -4.f)) - 1);
-  khi = min(T, klo + P.tof_wmax);
+  constexpr float m = 1.f / 64.f;
+  const float kt = (t - P.tof_e0) * P.tof_inv_w;
+  klo = max(0, (int)floorf(fmaxf(kt - P.tof_reach - m, -4.f)));
+  khi = min(T, (int)floorf(fminf(kt + P.tof_reach + m, (float)T + 4.f)) + 1);
 }
 
 template <int TT, int STRIDE>
@@ -928,6 +931,7 @@ static int views_for_launch(const DevPlan &P, int subset, const int *subset_dev)
 static void grad_shape(const DevPlan &P, long long nlor, int &K, int &split) {
   K = (P.T <= 1 && P.grad_k > 0) ? P.grad_k : 1;
   split = P.grad_split > 0 ? P.grad_split : split_for(nlor);
+  if (P.T > 1 && split > 4) split = 4;  // eight parts per LOR: non-TOF only
 }
 
 int grad_blocks_for(const DevPlan &P, int nv) {
@@ -954,13 +958,17 @@ cudaError_t launch_grad(const DevPlan &P, int subset, const int *subset_dev, con
   if (grid == 0) return cudaSuccess;
   note_launch();
   if (K == 4) {
-    if (split == 4) PET_GRAD_MP(4, 4);
+    if (split == 8) PET_GRAD_MP(4, 8);
+    else if (split == 4) PET_GRAD_MP(4, 4);
     else if (split == 2) PET_GRAD_MP(4, 2);
     else PET_GRAD_MP(4, 1);
   } else if (K == 2) {
-    if (split == 4) PET_GRAD_MP(2, 4);
+    if (split == 8) PET_GRAD_MP(2, 8);
+    else if (split == 4) PET_GRAD_MP(2, 4);
     else if (split == 2) PET_GRAD_MP(2, 2);
     else PET_GRAD_MP(2, 1);
+  } else if (split == 8) {
+    k_grad<1, 8><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
   } else if (split == 4) {
     PET_GRAD_LAUNCH(4);
   } else if (split == 2) {
