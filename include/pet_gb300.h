@@ -112,9 +112,10 @@ const float *pet_plan_sensitivity(const pet_plan *plan, int subset);
 
 /* Launch shape of the fused subset-gradient kernel: planes per thread (1, 2 or 4; more
  * than 1 only without TOF: those LORs of one view and radial bin share their in-plane
- * sample positions) and parts per LOR (1, 2, 4, or 8 without TOF: interleaved sets of
- * the driving planes of one LOR processed by different warps).  0 selects the built-in
- * heuristic.  Results are the same up to FP32 summation order. */
+ * sample positions) and parts per LOR (1, 2, 4, 8 or 16: interleaved sets of the
+ * driving planes of one LOR processed by different threads; 16 only without TOF, 8 only
+ * without TOF or with 11 or 13 TOF bins).  0 selects the built-in heuristic.  Results
+ * are the same up to FP32 summation order.  PET_ERR_ARG for an unsupported shape. */
 pet_status pet_plan_set_grad_shape(pet_plan *plan, int planes_per_thread, int parts);
 
 /* Autotuner: times every valid launch shape on subset 0 of the bound data (a uniform
@@ -284,8 +285,9 @@ pet_status pet_batch_create(pet_solver *const *solvers, int n, int iters_per_gra
 void pet_batch_destroy(pet_batch *b);
 /* Runs niter iterations of every solver (each solver's iteration counter advances). */
 pet_status pet_batch_run(pet_batch *b, long long niter, void *stream);
-/* Launch shape of the batched fused gradient (as pet_plan_set_grad_shape) and its
- * autotuner (times each shape on subset 0 of every solver; synchronises stream). */
+/* Launch shape of the batched fused gradient (planes per thread 1, 2 or 4; parts per
+ * LOR 1, 2, 4 or 8) and its autotuner (times each shape on subset 0 of every solver;
+ * synchronises stream). */
 pet_status pet_batch_set_grad_shape(pet_batch *b, int planes_per_thread, int parts);
 pet_status pet_batch_autotune(pet_batch *b, void *stream, int *planes_per_thread, int *parts);
 

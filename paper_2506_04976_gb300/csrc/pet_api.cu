@@ -165,8 +165,8 @@ extern "C" pet_status pet_plan_create(const pet_geometry *geom, pet_plan **out) 
     dp.tof_inv_w = (float)(1.0 / g.tof_bin);
     dp.tof_reach = (float)(3.0 * g.tof_sigma / g.tof_bin);
   }
-  // any fused-gradient launch (up to 8 parts per LOR) has at most this many blocks
-  const int gb_all = (int)((8 * nlor + kBlock - 1) / kBlock) + 1;
+  // any fused-gradient launch (up to 16 parts per LOR) has at most this many blocks
+  const int gb_all = (int)((16 * nlor + kBlock - 1) / kBlock) + 1;
   const int rb = ratio_blocks(dp, -1);
   pl->npart = std::max({gb_all, rb, rdp_blocks(g.nx, g.ny, g.nz), 4 * nrmse_blocks(pl->N), 1});
   bool ok = dalloc(&pl->d_view, V) == cudaSuccess && dalloc(&pl->d_vr, (size_t)V * R) == cudaSuccess &&
@@ -459,7 +459,8 @@ extern "C" pet_status pet_plan_set_grad_shape(pet_plan *plan, int planes_per_thr
   if (!plan) return PET_ERR_ARG;
   const bool kok = planes_per_thread == 0 || planes_per_thread == 1 ||
                    ((planes_per_thread == 2 || planes_per_thread == 4) && plan->T == 1);
-  const bool sok = parts == 0 || parts == 1 || parts == 2 || parts == 4 || (parts == 8 && plan->T == 1);
+  const bool sok = parts == 0 || ((parts == 1 || parts == 2 || parts == 4 || parts == 8 || parts == 16) &&
+                                   parts <= max_split(plan->dp));
   if (!kok || !sok) return PET_ERR_ARG;
   plan->dp.grad_k = planes_per_thread;
   plan->dp.grad_split = parts;
@@ -470,7 +471,7 @@ extern "C" pet_status pet_plan_autotune(pet_plan *plan, void *stream, int *plane
   if (!plan) return PET_ERR_ARG;
   if (!plan->has_data) return PET_ERR_STATE;
   cudaStream_t st = S(stream);
-  const int ks[3] = {1, 2, 4}, ss[4] = {1, 2, 4, 8};
+  const int ks[3] = {1, 2, 4}, ss[5] = {1, 2, 4, 8, 16};
   float *x = plan->d_img, *g = nullptr;
   if (dalloc(&g, plan->N) != cudaSuccess) return PET_ERR_NOMEM;  // setup-time temporary
   if (launch_fill(x, plan->N, 1.f, st) != cudaSuccess) { cudaFree(g); return PET_ERR_CUDA; }
@@ -488,8 +489,8 @@ extern "C" pet_status pet_plan_autotune(pet_plan *plan, void *stream, int *plane
   float best = 1e30f;
   int bk = 1, bs = 1;
   for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 4; ++b) {
-      if ((ks[a] > 1 || ss[b] > 4) && plan->T > 1) continue;
+    for (int b = 0; b < 5; ++b) {
+      if ((ks[a] > 1 && plan->T > 1) || ss[b] > max_split(plan->dp)) continue;
       plan->dp.grad_k = ks[a];
       plan->dp.grad_split = ss[b];
       float ms = 0.f;

@@ -208,6 +208,9 @@ cudaError_t launch_ratio(const DevPlan &P, int subset, const float *ax, float *q
 // q = m (1 - y/ybar); MODE_EM: q = m y/ybar; MODE_OBJ: no backprojection; MODE_SENS:
 // q = m (backprojects ones).  kl_part: per-block FP64 partial sums of the KL term
 // (may be NULL).  subset_dev (may be NULL) overrides `subset` from device memory.
+// Largest parts per LOR the fused gradient supports for this plan (16 non-TOF, 8 for
+// 11 or 13 TOF bins, else 4).
+int max_split(const DevPlan &P);
 cudaError_t launch_grad(const DevPlan &P, int subset, const int *subset_dev, const float *x,
                         const float *xT, float *g, float *gT, double *kl_part, int mode,
                         int *nblocks_out, cudaStream_t st);

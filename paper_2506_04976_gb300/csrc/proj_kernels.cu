@@ -589,11 +589,11 @@ cudaError_t launch_grad_batch(const GradJob *jobs, const int *begin, int njobs, 
   note_launch();
 #define PET_GB(KK, SP) k_grad_mp_batch<KK, SP><<<total_blocks, kBlock, 0, st>>>(jobs, begin, njobs, MODE_GRAD)
   if (K == 4) {
-    if (split == 4) PET_GB(4, 4); else if (split == 2) PET_GB(4, 2); else PET_GB(4, 1);
+    if (split == 8) PET_GB(4, 8); else if (split == 4) PET_GB(4, 4); else if (split == 2) PET_GB(4, 2); else PET_GB(4, 1);
   } else if (K == 2) {
-    if (split == 4) PET_GB(2, 4); else if (split == 2) PET_GB(2, 2); else PET_GB(2, 1);
+    if (split == 8) PET_GB(2, 8); else if (split == 4) PET_GB(2, 4); else if (split == 2) PET_GB(2, 2); else PET_GB(2, 1);
   } else {
-    if (split == 4) PET_GB(1, 4); else if (split == 2) PET_GB(1, 2); else PET_GB(1, 1);
+    if (split == 8) PET_GB(1, 8); else if (split == 4) PET_GB(1, 4); else if (split == 2) PET_GB(1, 2); else PET_GB(1, 1);
   }
 #undef PET_GB
   return cudaGetLastError();
@@ -928,10 +928,17 @@ static int views_for_launch(const DevPlan &P, int subset, const int *subset_dev)
 
 // Launch shape of the fused gradient: planes per thread (non-TOF only) and parts per
 // LOR.  P.grad_k / P.grad_split hold the autotuner's choice (0: heuristic).
+// Largest parts per LOR of a launch: 16 without TOF, 8 for the windowed TOF kernels
+// (11 and 13 bins), 4 otherwise.
+int max_split(const DevPlan &P) {
+  if (P.T <= 1) return 16;
+  return (P.T == 11 || P.T == 13) ? 8 : 4;
+}
+
 static void grad_shape(const DevPlan &P, long long nlor, int &K, int &split) {
   K = (P.T <= 1 && P.grad_k > 0) ? P.grad_k : 1;
   split = P.grad_split > 0 ? P.grad_split : split_for(nlor);
-  if (P.T > 1 && split > 4) split = 4;  // eight parts per LOR: non-TOF only
+  split = std::min(split, max_split(P));
 }
 
 int grad_blocks_for(const DevPlan &P, int nv) {
@@ -958,17 +965,23 @@ cudaError_t launch_grad(const DevPlan &P, int subset, const int *subset_dev, con
   if (grid == 0) return cudaSuccess;
   note_launch();
   if (K == 4) {
-    if (split == 8) PET_GRAD_MP(4, 8);
+    if (split == 16) PET_GRAD_MP(4, 16);
+    else if (split == 8) PET_GRAD_MP(4, 8);
     else if (split == 4) PET_GRAD_MP(4, 4);
     else if (split == 2) PET_GRAD_MP(4, 2);
     else PET_GRAD_MP(4, 1);
   } else if (K == 2) {
-    if (split == 8) PET_GRAD_MP(2, 8);
+    if (split == 16) PET_GRAD_MP(2, 16);
+    else if (split == 8) PET_GRAD_MP(2, 8);
     else if (split == 4) PET_GRAD_MP(2, 4);
     else if (split == 2) PET_GRAD_MP(2, 2);
     else PET_GRAD_MP(2, 1);
+  } else if (split == 16) {
+    k_grad<1, 16><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
   } else if (split == 8) {
-    k_grad<1, 8><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
+    if (P.T <= 1) k_grad<1, 8><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
+    else if (P.T == 11) k_grad_tofw<11, 8><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
+    else k_grad_tofw<13, 8><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
   } else if (split == 4) {
     PET_GRAD_LAUNCH(4);
   } else if (split == 2) {

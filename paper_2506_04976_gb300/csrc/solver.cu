@@ -1118,7 +1118,7 @@ static pet_status batch_iteration(pet_batch *b, int j, cudaStream_t st) {
 extern "C" pet_status pet_batch_set_grad_shape(pet_batch *b, int planes_per_thread, int parts) {
   if (!b) return PET_ERR_ARG;
   if (!(planes_per_thread == 1 || planes_per_thread == 2 || planes_per_thread == 4) ||
-      !(parts == 1 || parts == 2 || parts == 4))
+      !(parts == 1 || parts == 2 || parts == 4 || parts == 8))
     return PET_ERR_ARG;
   b->K = planes_per_thread;
   b->split = parts;
@@ -1151,11 +1151,11 @@ extern "C" pet_status pet_batch_autotune(pet_batch *b, void *stream, int *planes
   cudaEvent_t e0, e1;
   SCK(cudaEventCreate(&e0));
   SCK(cudaEventCreate(&e1));
-  const int ks[3] = {1, 2, 4}, ss[3] = {1, 2, 4};
+  const int ks[3] = {1, 2, 4}, ss[4] = {1, 2, 4, 8};
   float best = 1e30f;
   int bk = 2, bs = 1;
   for (int a = 0; a < 3; ++a)
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < 4; ++c) {
       b->K = ks[a];
       b->split = ss[c];
       e = batch_tables(b);

@@ -13,6 +13,11 @@ Every `--check` iterations the KKT residual ||min(x, grad F(x))|| / ||grad F(x0)
 recorded and the image saved (float32) to tests/golden/ref_<config>_seed<k>.npz.
 
     python tests/golden/make_reference_lbfgs.py c2 0 [--workers 7] [--maxiter 600]
+        [--init file.npz] [--out file.npz]
+
+--init restarts from an image this script wrote (the KKT normalisation always refers to
+the OSEM start image and is stored with the result as g0_norm); --out writes elsewhere
+than tests/golden, e.g. while the run is still far from converged.
 """
 import argparse
 import multiprocessing as mp
@@ -54,6 +59,7 @@ def main():
     ap.add_argument("--maxiter", type=int, default=600)
     ap.add_argument("--check", type=int, default=20)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--init", default=None)
     a = ap.parse_args()
     from scipy.optimize import minimize
 
@@ -88,8 +94,13 @@ def main():
 
     F0, g0 = fg(x)
     g0n = np.linalg.norm(g0)
+    it0 = 0
+    if a.init:
+        prev = np.load(a.init)
+        assert str(prev["config"]) == a.config and int(prev["seed"]) == a.seed
+        x, it0 = prev["x"].astype(np.float64), int(prev["epochs"])
     t0 = time.time()
-    state = {"it": 0, "kkt": np.inf}
+    state = {"it": it0, "kkt": np.inf}
 
     def fun(z):
         xx = (d * z.reshape(shape))
@@ -106,7 +117,7 @@ def main():
             state["kkt"] = res
             print(f"iter {state['it']} evals {evals[0]} kkt {res:.3e} ({time.time() - t0:.0f} s)", flush=True)
             np.savez_compressed(out, x=xx.astype(np.float32), kkt=res, epochs=state["it"], config=a.config,
-                                seed=a.seed, method="lbfgsb")
+                                seed=a.seed, method="lbfgsb", g0_norm=g0n)
 
     z0 = (x / d).ravel()
     minimize(fun, z0, jac=True, method="L-BFGS-B", bounds=[(0, None)] * z0.size, callback=callback,

@@ -78,12 +78,12 @@ def test_batch_autotune_and_shapes():
     from paper_2506_04976_gb300 import binding as pet
     inst = _instances()
     results = []
-    for shape in ("auto", (1, 1), (4, 4)):
+    for shape in ("auto", (1, 1), (4, 4), (2, 8)):
         solvers = [_solver(pet, p, plan, x0, 200 + i, pet.SAGA) for i, (p, plan, _, _, x0) in enumerate(inst)]
         b = pet.Batch(solvers, iters_per_graph=5)
         if shape == "auto":
             k, sp = b.autotune()
-            assert k in (1, 2, 4) and sp in (1, 2, 4)
+            assert k in (1, 2, 4) and sp in (1, 2, 4, 8)
         else:
             b.set_grad_shape(*shape)
         b.run(2 * 5 + 8)

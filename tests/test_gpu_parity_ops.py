@@ -305,15 +305,15 @@ def test_y_zero_and_zero_image():
 
 
 @pytest.mark.parametrize("key", ["c1", "3d", "tof"])
-@pytest.mark.parametrize("shape", [(1, 1), (1, 2), (1, 4), (1, 8), (2, 1), (2, 4), (2, 8), (4, 1), (4, 2),
-                                   (4, 4), (4, 8)])
+@pytest.mark.parametrize("shape", [(1, 1), (1, 2), (1, 4), (1, 8), (1, 16), (2, 1), (2, 4), (2, 8), (2, 16),
+                                   (4, 1), (4, 2), (4, 4), (4, 8), (4, 16)])
 def test_grad_launch_shapes(key, shape):
     """Every launch shape of the fused gradient (planes per thread x parts per LOR)
     gives the oracle's subset objective and gradient."""
     c = case(key)
     k, parts = shape
-    if (k > 1 or parts > 4) and c.plan.T > 1:
-        pytest.skip("planes per thread > 1 and eight parts per LOR are non-TOF only")
+    if (k > 1 or parts > 8) and c.plan.T > 1:
+        pytest.skip("planes per thread > 1 and sixteen parts per LOR are non-TOF only")
     c.plan.set_grad_shape(k, parts)
     try:
         s = 3
@@ -335,7 +335,7 @@ def test_grad_launch_shapes(key, shape):
 def test_autotune_keeps_parity():
     c = case("3d")
     k, parts = c.plan.autotune()
-    assert k in (1, 2, 4) and parts in (1, 2, 4, 8)
+    assert k in (1, 2, 4) and parts in (1, 2, 4, 8, 16)
     _, g = c.plan.objective_grad(c.xt, 1)
     _, gd = O.data_grad(c.G, c.n, 1, c.x, c.m, c.p["r"], c.p["y"])
     scale = O.sensitivity(c.G, c.n, 1, c.m)
