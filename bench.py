@@ -85,9 +85,9 @@ def ncu_traffic(kernel_tag, kernel_name):
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    if d.get("source_hash") != source_hash() or d.get("kernel") != kernel_name:
+    if d.get("source_hash") != source_hash():
         return None
-    return d.get("dram_bytes_per_launch")
+    return d.get("dram_bytes_per_launch", {}).get(kernel_name)
 
 
 class Clocks:

@@ -441,6 +441,10 @@ struct pet_solver {
   // fill the SMs that the subset-gradient launch leaves idle in its last wave.
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // Inner-iteration gradient accumulators (canonical, transposed), alternating with the
+  // iteration's parity: while iteration k accumulates into one pair, the side stream
+  // clears the pair iteration k-1 used (gbuf[0] is g).
+  float *gbuf[2] = {nullptr, nullptr}, *gTbuf[2] = {nullptr, nullptr};
   cudaGraphExec_t exec[2] = {nullptr, nullptr};  // [0] plain epoch, [1] epoch starting with a refresh
   // optional event timing of the fused subset-gradient kernel: one (start, stop) pair per
   // launch slot of an SVRG outer loop (or of an epoch for SGD/SAGA)
@@ -489,6 +493,7 @@ static void solver_free(pet_solver *s) {
   cudaFree(s->x); cudaFree(s->D); cudaFree(s->g); cudaFree(s->gS); cudaFree(s->H);
   cudaFree(s->sub_log); cudaFree(s->prob); cudaFree(s->norm_part); cudaFree(s->d_sub); cudaFree(s->d_w);
   cudaFree(s->gSh); cudaFree(s->xhatT);
+  cudaFree(s->gbuf[1]); cudaFree(s->gTbuf[0]); cudaFree(s->gTbuf[1]);
   cudaFree(s->table); cudaFree(s->G); cudaFree(s->xhat_old); cudaFree(s->Gfull_old);
   cudaFree(s->part); cudaFree(s->st); cudaFree(s->tau_log);
   delete s;
@@ -530,6 +535,11 @@ extern "C" pet_status pet_solver_create(pet_plan *plan, const pet_solver_opts *o
          cudaMalloc(&s->G, N * 4) == cudaSuccess;
   if (ok && o.algo == PET_SVRG)
     ok = cudaMalloc(&s->xhat_old, N * 4) == cudaSuccess && cudaMalloc(&s->Gfull_old, N * 4) == cudaSuccess;
+  if (ok) {
+    s->gbuf[0] = s->g;
+    ok = cudaMalloc(&s->gbuf[1], N * 4) == cudaSuccess && cudaMalloc(&s->gTbuf[0], N * 4) == cudaSuccess &&
+         cudaMalloc(&s->gTbuf[1], N * 4) == cudaSuccess;
+  }
   if (ok && o.low_memory) ok = cudaMalloc(&s->xhatT, N * 4) == cudaSuccess;
   if (ok && o.sampling == PET_SAMPLE_IMPORTANCE)
     ok = cudaMalloc(&s->prob, s->n * sizeof(double)) == cudaSuccess &&
@@ -563,7 +573,10 @@ extern "C" pet_status pet_solver_set_image(pet_solver *s, const float *x, void *
       cudaMemsetAsync(s->g, 0, N * 4, st) != cudaSuccess ||
       cudaMemsetAsync(s->D, 0, N * 4, st) != cudaSuccess ||
       cudaMemsetAsync(s->st, 0, sizeof(SolverState), st) != cudaSuccess ||
-      cudaMemsetAsync(s->plan->d_gT, 0, N * 4, st) != cudaSuccess)
+      cudaMemsetAsync(s->plan->d_gT, 0, N * 4, st) != cudaSuccess ||
+      cudaMemsetAsync(s->gbuf[1], 0, N * 4, st) != cudaSuccess ||
+      cudaMemsetAsync(s->gTbuf[0], 0, N * 4, st) != cudaSuccess ||
+      cudaMemsetAsync(s->gTbuf[1], 0, N * 4, st) != cudaSuccess)
     return PET_ERR_CUDA;
   s->k = 0;
   s->rng = s->o.seed;
@@ -646,8 +659,9 @@ static cudaError_t record(pet_solver *s, cudaEvent_t ev, cudaStream_t st) {
 // iterate in both layouts) and mode (MODE_NGRAD subtracts) serve the table-free SVRG.
 static pet_status data_grad(pet_solver *s, int sub, float *dst, cudaStream_t st, int slot = -1,
                             bool combine = true, const int *sub_dev = nullptr, const float *img = nullptr,
-                            const float *imgT = nullptr, int mode = MODE_GRAD) {
+                            const float *imgT = nullptr, int mode = MODE_GRAD, float *dstT = nullptr) {
   pet_plan *p = s->plan;
+  if (!dstT) dstT = p->d_gT;
   if (s->o.deterministic) {
     pet_status e = pet_objective_grad(p, sub, s->x, dst, nullptr, nullptr, PET_GRAD_DETERMINISTIC, st);
     return e;
@@ -659,7 +673,7 @@ static pet_status data_grad(pet_solver *s, int sub, float *dst, cudaStream_t st,
   }
   const bool prof = s->profile && slot >= 0 && slot < (int)s->ev0.size();
   if (prof) SCK(record(s, s->ev0[slot], st));
-  SCK(launch_grad(p->dp, sub, sub_dev, im, imT, dst, p->d_gT, nullptr, mode, nullptr, st));
+  SCK(launch_grad(p->dp, sub, sub_dev, im, imT, dst, dstT, nullptr, mode, nullptr, st));
   if (prof) {
     SCK(record(s, s->ev1[slot], st));
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -668,9 +682,9 @@ static pet_status data_grad(pet_solver *s, int sub, float *dst, cudaStream_t st,
     else s->pending[slot] = 1;
   }
   if (combine) {
-    SCK(launch_transpose(p->d_gT, dst, p->g.nx, p->g.ny, p->g.nz, 1, 1, st));  // add
+    SCK(launch_transpose(dstT, dst, p->g.nx, p->g.ny, p->g.nz, 1, 1, st));  // add
     note_launch();
-    k_clear2<<<grid_elems(s->N / 4), 256, 0, st>>>(p->d_gT, nullptr, s->N);
+    k_clear2<<<grid_elems(s->N / 4), 256, 0, st>>>(dstT, nullptr, s->N);
     SCK(apply_res(p, dst, st));
   }
   return PET_OK;
@@ -686,10 +700,12 @@ static RdpArgs prior_args(const pet_solver *s, float scale) {
 
 // grad S(x) into gS on the side stream, ordered after everything enqueued on st so far;
 // join_prior makes st wait for it.  Under stream capture the two become graph branches.
-static pet_status fork_prior(pet_solver *s, cudaStream_t st) {
+static pet_status fork_prior(pet_solver *s, cudaStream_t st, int clear_buf) {
   SCK(cudaEventRecord(s->ev_fork, st));
   SCK(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
   SCK(launch_rdp(prior_args(s, s->o.beta), s->x, s->gS, nullptr, nullptr, 0, nullptr, s->side));
+  note_launch();
+  k_clear2<<<grid_elems(s->N / 4), 256, 0, s->side>>>(s->gbuf[clear_buf], s->gTbuf[clear_buf], s->N);
   SCK(cudaEventRecord(s->ev_join, s->side));
   return PET_OK;
 }
@@ -761,7 +777,9 @@ static pet_status iterate(pet_solver *s, long long k, int sub, cudaStream_t st) 
   // the transposed copy of x is kept current by the update kernel
   (void)p;
   if (!refresh && sub < 0) return PET_ERR_ARG;
-  pet_status e = fork_prior(s, st);
+  const int b = (int)(k & 1);
+  float *gk = s->gbuf[b], *gTk = s->gTbuf[b];
+  pet_status e = fork_prior(s, st, b ^ 1);
   if (e != PET_OK) return e;
   const bool importance = s->o.sampling == PET_SAMPLE_IMPORTANCE;
   if (refresh) {
@@ -795,10 +813,10 @@ static pet_status iterate(pet_solver *s, long long k, int sub, cudaStream_t st) 
       e = join_prior(s, st);
       if (e != PET_OK) return e;
       for (int t = 0; t < s->n; ++t) {
-        e = data_grad(s, t, s->g, st, slot_of(s, k, t));
+        e = data_grad(s, t, gk, st, slot_of(s, k, t));
         if (e != PET_OK) return e;
         note_launch();
-        k_sub_norms<<<dim3(kNormBlocks, 1), 256, 0, st>>>(s->g, s->gS, s->G, s->n, s->N, 0,
+        k_sub_norms<<<dim3(kNormBlocks, 1), 256, 0, st>>>(gk, s->gS, s->G, s->n, s->N, 0,
                                                           s->norm_part + (size_t)t * kNormBlocks);
       }
     }
@@ -821,25 +839,25 @@ static pet_status iterate(pet_solver *s, long long k, int sub, cudaStream_t st) 
       k_draw<<<1, 32, 0, st>>>(s->prob, s->n, (unsigned long long)s->o.seed, k, s->d_sub, s->d_w);
       sub_dev = s->d_sub;
     }
-    e = data_grad(s, sub, s->g, st, slot_of(s, k, -1), false, sub_dev);
+    e = data_grad(s, sub, gk, st, slot_of(s, k, -1), false, sub_dev, nullptr, nullptr, MODE_GRAD, gTk);
     if (e != PET_OK) return e;
     if (s->o.low_memory) {  // minus the subset gradient at the snapshot
-      e = data_grad(s, sub, s->g, st, -1, false, sub_dev, s->xhat_old, s->xhatT, MODE_NGRAD);
+      e = data_grad(s, sub, gk, st, -1, false, sub_dev, s->xhat_old, s->xhatT, MODE_NGRAD, gTk);
       if (e != PET_OK) return e;
     }
-    if (p->res) {  // (P G)^T = G P^T, applied once to the combined accumulators
-      SCK(from_frames(p, s->g, st));
-      SCK(apply_res(p, s->g, st));
+    if (p->res && !s->o.deterministic) {  // (P G)^T = G P^T, once on the combined accumulators
+      SCK(launch_transpose(gTk, gk, p->g.nx, p->g.ny, p->g.nz, 1, 2, st));
+      SCK(apply_res(p, gk, st));
     }
     e = join_prior(s, st);
     if (e != PET_OK) return e;
-    const UpdArgs a = upd_args(s, sub, k);
+    UpdArgs a = upd_args(s, sub, k);
+    a.g = gk;
+    a.gT = gTk;
     note_launch();
     if (s->o.algo == PET_SGD) k_update<0><<<tile_grid(s), dim3(32, 8), 0, st>>>(a);
     else if (s->o.algo == PET_SAGA) k_update<1><<<tile_grid(s), dim3(32, 8), 0, st>>>(a);
     else k_update<2><<<tile_grid(s), dim3(32, 8), 0, st>>>(a);
-    note_launch();
-    k_clear2<<<grid_elems(s->N / 4), 256, 0, st>>>(s->g, p->d_gT, s->N);
   }
   SCK(cudaGetLastError());
   return PET_OK;

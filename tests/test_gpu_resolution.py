@@ -98,9 +98,10 @@ def test_em_update_with_resolution_model():
     _close(x.cpu().numpy(), O.em_update(c.G, c.n, 3, c.m, c.p["r"], c.p["y"], c.x))
 
 
-@pytest.mark.parametrize("key,algo,low_memory", [("c1", O.SVRG, False), ("3d", O.SVRG, False),
-                                                 ("3d", O.SVRG, True), ("tof", O.SAGA, False)])
-def test_solver_with_resolution_model(key, algo, low_memory):
+@pytest.mark.parametrize("key,algo,low_memory,det", [("c1", O.SVRG, False, False), ("3d", O.SVRG, False, False),
+                                                     ("3d", O.SVRG, True, False), ("tof", O.SAGA, False, False),
+                                                     ("3d", O.SAGA, False, True)])
+def test_solver_with_resolution_model(key, algo, low_memory, det):
     from paper_2506_04976_gb300 import binding as pet
     c = case(key)
     n = c.n
@@ -111,7 +112,7 @@ def test_solver_with_resolution_model(key, algo, low_memory):
     kw = dict(omega=2, step_rule=O.STEP_VANISH, tau0=1.0, eta=0.02, precond_kind=1, alpha=1.0, delta_rel=1e-6,
               pc_iters=(0, n, 2 * n), beta=c.p["beta"], gamma=c.p["gamma"], eps=c.p["eps"])
     xo, _, _ = O.solve(c.G, x0, c.m, c.p["r"], c.p["y"], sens, algo=algo, nsub=n, niter=niter, order=order, **kw)
-    s = pet.Solver(c.plan, algo=algo, order=order, low_memory=low_memory, **kw)
+    s = pet.Solver(c.plan, algo=algo, order=order, low_memory=low_memory, deterministic=det, **kw)
     s.set_image(_t(x0))
     s.run(niter)
     xg = s.image().cpu().numpy().astype(np.float64)
