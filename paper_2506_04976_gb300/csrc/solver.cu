@@ -1230,6 +1230,15 @@ extern "C" pet_status pet_batch_run(pet_batch *b, long long niter, void *stream)
       done += 1;
       continue;
     }
+    // A single-solver iteration leaves its accumulator pair for the next one to clear;
+    // the batched phases use (g, the plan's transposed accumulator), so clear it here.
+    for (pet_solver *s : b->s) {
+      if (s->k <= 0) continue;
+      const int pb = (int)((s->k - 1) & 1);
+      note_launch();
+      k_clear2<<<grid_elems(s->N / 4), 256, 0, st>>>(s->gbuf[pb], s->gTbuf[pb], s->N);
+    }
+    SCK(cudaGetLastError());
     if (!b->exec) {
       cudaGraph_t graph = nullptr;
       const long long before = launch_count();
