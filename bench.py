@@ -52,6 +52,8 @@ def parse():
                     help="grad mode: 'auto' (autotuner) or 'K,S' planes per thread, parts per LOR")
     ap.add_argument("--config", default="c2", choices=["c2", "c3"],
                     help="grad mode: c2 (non-TOF, 1e7 counts) or c3 (11 TOF bins, 1e6 counts)")
+    ap.add_argument("--study-config", default="c1", choices=["c1", "c2"],
+                    help="study mode: workload with a converged reference image in tests/golden")
     return ap.parse_args()
 
 
@@ -318,25 +320,33 @@ def run_configs(args, pet, dev):
         r["hbm_frac"] = r["achieved_gbs"] / peak
         if T > 1:
             r["tof_bins_per_s"] = lors * T / (r["fused_kernel_ms"] * 1e-3)
+        if not args.no_cpu:  # the FP64 oracle on one or two whole subset gradients of the same workload
+            times = cpu_baseline(p, 0, steps=1 if T > 1 else 2)
+            r["cpu_oracle"] = {"subset_grads_per_s": len(times) / sum(times), "cores": 1,
+                               "sample": f"{len(times)} subset gradient(s), FP64, 1 thread"}
         out["configs"][cfg] = r
     print(json.dumps(out), flush=True)
 
 
 def run_study(args, pet, dev, max_epochs=1500):
-    """The comparison of Sec. 3.2 (Fig. 2) on the 2D workload against its converged oracle
-    image: SGD / SAGA / SVRG x MLEM / harmonic preconditioner x tau0 in {0.3, 1, 1.5},
-    vanishing steps (eta = 0.02), preconditioner updated in epochs 1-3, subsets without
-    replacement; epochs and GPU seconds from the OSEM start to NRMSE < 1%."""
+    """The comparison of Sec. 3.2 (Fig. 2) against a converged oracle image (2D workload by
+    default, 3D with --study-config c2): SGD / SAGA / SVRG x MLEM / harmonic preconditioner
+    x tau0 in {0.3, 1, 1.5}, vanishing steps (eta = 0.02), preconditioner updated in epochs
+    1-3, subsets without replacement; epochs and GPU seconds from the OSEM start to
+    NRMSE < 1%."""
     import torch
     from paper_2506_04976_gb300 import synth
-    ref_path = os.path.join(ROOT, "tests", "golden", "ref_c1_seed0.npz")
+    cfg = args.study_config
+    ref_path = os.path.join(ROOT, "tests", "golden", f"ref_{cfg}_seed0.npz")
     ref = np.load(ref_path)
-    p = synth.make_problem("c1", 0)
+    p = synth.make_problem(cfg, 0)
     n = p["nsub"]
     plan = pet.Plan(p["geom"], n)
-    plan.set_data(torch.from_numpy(p["y"].astype(np.int32)).to(dev), torch.from_numpy(p["r"]).to(dev),
+    y = p["y"].view(np.int16) if p["y"].dtype == np.uint16 else p["y"].astype(np.int32)
+    plan.set_data(torch.from_numpy(y).to(dev), torch.from_numpy(p["r"]).to(dev),
                   torch.from_numpy(p["mu"].astype(np.float32)).to(dev),
                   torch.from_numpy(p["sens"].astype(np.float32)).to(dev))
+    plan.autotune()
     xref = torch.from_numpy(ref["x"]).to(dev)
     mask = torch.from_numpy(p["mask"]).to(dev)
     bg = torch.from_numpy(p["bg"]).to(dev)
@@ -367,7 +377,7 @@ def run_study(args, pet, dev, max_epochs=1500):
                 torch.cuda.synchronize()
                 rows.append({"algo": aname, "precond": pname, "tau0": tau0, "epochs_to_1pct": reached,
                              "seconds": a.elapsed_time(b) / 1e3, "final_nrmse": val})
-    print(json.dumps({"mode": "study", "workload": "c1 (2D, n = 6, beta = 0.1)", "max_epochs": max_epochs,
+    print(json.dumps({"mode": "study", "workload": f"{cfg}, n = {n}, beta = {p['beta']:.4g}", "max_epochs": max_epochs,
                       "reference_kkt": float(ref["kkt"]), "runs": rows}), flush=True)
 
 
