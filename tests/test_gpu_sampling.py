@@ -141,3 +141,30 @@ def test_invalid_combinations_rejected():
     with pytest.raises(pet.PetError) as e:
         pet.Solver(plan, algo=pet.SVRG, low_memory=True, deterministic=True)
     assert e.value.status == 6
+
+
+@pytest.mark.parametrize("name", ["ALG1", "ALG2", "ALG3"])
+def test_table1_presets_match_oracle(name):
+    """The submitted algorithms' settings (Table 1) run by the CUDA solver and by the
+    oracle with the same subset order: stepsizes within 1e-3 relative (BB steps are
+    ratios of FP64 dot products of differences of FP32 images) and images within 1e-3."""
+    from paper_2506_04976_gb300 import binding as pet
+    from paper_2506_04976_gb300.presets import petric_solver_kwargs
+    key = "3d"
+    p, plan, G, m, sens, x0 = problem(key)
+    n = p["nsub"]
+    kw = petric_solver_kwargs(name, n)
+    niter = 7 * n + 1  # past the ALG2 cap change at k = 2n and the epoch-6 preconditioner update
+    seed = 9
+    rule = O.SAMPLE_COFACTOR if kw["sampling"] == pet.SAMPLE_COFACTOR else O.SAMPLE_PERM
+    order = O.subset_order(seed, n, niter, rule)
+    s = pet.Solver(plan, seed=seed, beta=p["beta"], gamma=p["gamma"], eps=p["eps"], **kw)
+    s.set_image(torch.from_numpy(x0).to(DEV))
+    s.run(niter)
+    xg = s.image().cpu().numpy().astype(np.float64)
+    okw = {k: v for k, v in kw.items() if k not in ("algo", "sampling")}
+    xo, to, _ = O.solve(G, x0, m, p["r"], p["y"], sens, algo=O.SVRG, nsub=n, niter=niter, order=order,
+                        beta=p["beta"], gamma=p["gamma"], eps=p["eps"], **okw)
+    assert np.array_equal(s.subsets(), np.where(np.arange(niter) % (2 * n) == 0, -1, order))
+    assert np.allclose(s.taus(), to, rtol=1e-3)
+    assert np.linalg.norm(xg - xo) <= 1e-3 * np.linalg.norm(xo)
