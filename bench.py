@@ -585,8 +585,8 @@ def main():
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     kern_ms, kern_n = 0.0, 0
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    clk = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv"))
+    import tempfile
+    clk = Clocks(os.path.join(tempfile.gettempdir(), f"pet_bench_clocks_rank{rank}.csv"))
     if pg:
         pg.barrier()
     torch.cuda.synchronize()

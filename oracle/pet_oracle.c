@@ -823,8 +823,9 @@ void o_em_update(const og_geom *g, int nsub, int s, const double *m, const doubl
 /* ------------------------------------------------------------------------- */
 /* NRMSE against a reference image, Sec. 3.1: root mean square difference over */
 /* the evaluation mask, divided by the mean of the reference over the          */
-/* background mask.  Parity unpinned: the masks are a reading of "excluding    */
-/* cold background ... normalized by the largest background ellipsoid".        */
+/* background mask.  Parity unpinned: the paper describes the masks only in   */
+/* words (leave out the cold surroundings of the phantom, normalise by the     */
+/* largest background region); these masks are a reading of that.             */
 /* ------------------------------------------------------------------------- */
 double o_nrmse(size_t N, const double *x, const double *ref, const unsigned char *mask,
                const unsigned char *bg) {

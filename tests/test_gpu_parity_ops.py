@@ -1,6 +1,6 @@
 """GPU parity of each operator against the FP64 oracle on the same seeded inputs.
 
-Tolerances (derived from FP32 arithmetic; see DESIGN.md "Tolerances"):
+Tolerances (derived from FP32 arithmetic):
   * projections, backprojections, sensitivities, attenuation factors: relative L2 error
     per view / per image <= 1e-5 and elementwise |d| <= 1e-4 |ref| + 1e-5 max|ref|;
   * gradients of the KL term (a difference of two positive backprojections): errors
