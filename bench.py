@@ -64,6 +64,21 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(pg, seconds, device):
+    """The slowest rank's time (all ranks call this; pg None: single process)."""
+    if pg is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t)
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units processed by all ranks (independent replicas) per second of the slowest rank."""
+    return units_per_rank * world / seconds
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -608,13 +623,8 @@ def main():
     if pg:
         pg.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_total = sum(step_ms) / 1e3
-    if pg:
-        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t_total = float(tt)
-    units = grads_per_step * args.steps * world
-    value = units / t_total
+    t_total = max_over_ranks(pg, sum(step_ms) / 1e3, dev)
+    value = whole_job_rate(grads_per_step * args.steps, world, t_total)
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
@@ -633,12 +643,8 @@ def main():
             xo.copy_(solver.image(), non_blocking=True)
         b.record()
         torch.cuda.synchronize()
-        te = a.elapsed_time(b) / 1e3
-        if pg:
-            tt = torch.tensor([te], device=dev, dtype=torch.float64)
-            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-            te = float(tt)
-        e2e = {"value": grads_per_step * args.steps * world / te, "unit": UNIT,
+        te = max_over_ranks(pg, a.elapsed_time(b) / 1e3, dev)
+        e2e = {"value": whole_job_rate(grads_per_step * args.steps, world, te), "unit": UNIT,
                "h2d_bytes_per_step": int(y_host.numel() * 2 + r_host.numel() * 4 + x0_host.numel() * 4),
                "d2h_bytes_per_step": int(xo.numel() * 4)}
         solver.kernel_time()
