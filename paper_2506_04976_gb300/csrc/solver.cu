@@ -459,16 +459,21 @@ struct pet_solver {
 
 static pet_status grow_tau_log(pet_solver *s, long long need) {
   if (need <= s->tau_cap) return PET_OK;
+  // Rare (capacity doubles): wait for every launch that may still write the old logs,
+  // whatever stream the caller used, before copying them.
+  if (cudaDeviceSynchronize() != cudaSuccess) return PET_ERR_CUDA;
   long long cap = std::max(need, 2 * s->tau_cap + 1024);
   double *nl = nullptr;
   int *ns = nullptr;
   if (cudaMalloc(&nl, cap * sizeof(double)) != cudaSuccess) return PET_ERR_NOMEM;
   if (cudaMalloc(&ns, cap * sizeof(int)) != cudaSuccess) { cudaFree(nl); return PET_ERR_NOMEM; }
-  cudaMemset(nl, 0, cap * sizeof(double));
-  cudaMemset(ns, 0xff, cap * sizeof(int));
+  bool ok = cudaMemset(nl, 0, cap * sizeof(double)) == cudaSuccess &&
+            cudaMemset(ns, 0xff, cap * sizeof(int)) == cudaSuccess;
+  if (ok && s->tau_log)
+    ok = cudaMemcpy(nl, s->tau_log, s->tau_cap * sizeof(double), cudaMemcpyDeviceToDevice) == cudaSuccess &&
+         cudaMemcpy(ns, s->sub_log, s->tau_cap * sizeof(int), cudaMemcpyDeviceToDevice) == cudaSuccess;
+  if (!ok) { cudaFree(nl); cudaFree(ns); return PET_ERR_CUDA; }
   if (s->tau_log) {
-    cudaMemcpy(nl, s->tau_log, s->tau_cap * sizeof(double), cudaMemcpyDeviceToDevice);
-    cudaMemcpy(ns, s->sub_log, s->tau_cap * sizeof(int), cudaMemcpyDeviceToDevice);
     cudaFree(s->tau_log);
     cudaFree(s->sub_log);
   }
