@@ -52,7 +52,7 @@ def parse():
                     help="grad mode: 'auto' (autotuner) or 'K,S' planes per thread, parts per LOR")
     ap.add_argument("--config", default="c2", choices=["c2", "c3"],
                     help="grad mode: c2 (non-TOF, 1e7 counts) or c3 (11 TOF bins, 1e6 counts)")
-    ap.add_argument("--study-config", default="c1", choices=["c1", "c2"],
+    ap.add_argument("--study-config", default="c1", choices=["c1", "c2", "c2s", "c2s16"],
                     help="study mode: workload with a converged reference image in tests/golden")
     return ap.parse_args()
 
@@ -685,7 +685,7 @@ def main():
     clocks = clk.summary()
     nrmse_times = {}
     if not args.no_nrmse:
-        for cfg in ("c1", "c2"):
+        for cfg in ("c1", "c2", "c2s"):
             t = time_to_nrmse(pet, dev, cfg)
             if t is not None:
                 nrmse_times[cfg] = t

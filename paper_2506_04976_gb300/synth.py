@@ -334,8 +334,17 @@ def _smooth(a, sigma):
     return gaussian_filter(a, sigma, mode="nearest")
 
 
+# Smaller 3D workloads for convergence studies (the c2 brain and scanner at half the
+# resolution in every direction: 64x64x23 voxels of 4x4x5.7 mm, 125 radial bins x 84
+# views, 21 subsets of 4 views), with the relative prior strength 4 ("c2s") or 16.
+STUDY_WORKLOADS = {"c2s": dict(nx=64, nz=23, nrad=125, nview=84, nsub=21),
+                   "c2s16": dict(nx=64, nz=23, nrad=125, nview=84, nsub=21, beta=16 * 2e-4 * 1e7 / 3e7)}
+
+
 def _setup(name: str, seed: int, **over):
     """Geometry, phantom and reconstruction parameters of a workload (no data)."""
+    if name in STUDY_WORKLOADS:
+        return _setup("c2", seed, **{**STUDY_WORKLOADS[name], **over})
     if name == "c1":
         nx = over.get("nx", 64)
         geom = dict(nx=nx, ny=nx, nz=1, dx=2.0 * 64 / nx, dy=2.0 * 64 / nx, dz=2.0,
