@@ -207,7 +207,8 @@ typedef enum {
   PET_STEP_CONST = 0,  /* tau0 */
   PET_STEP_VANISH = 1, /* tau0 / (1 + eta k / n)          (Sec. 2.2) */
   PET_STEP_ALG1 = 2,   /* piecewise 3, 2, 1.5, 1, 0.5      (Table 1, ALG1) */
-  PET_STEP_BB = 3,     /* short Barzilai-Borwein p'q/q'q at SVRG refreshes (Sec. 2.2) */
+  PET_STEP_BB = 3,     /* short Barzilai-Borwein step at SVRG refreshes (Sec. 2.2), in the
+                          metric of the preconditioner D: p'q / q'Dq */
   PET_STEP_ALG2 = 4    /* BB capped at 3 / 2.2 / 1         (Table 1, ALG2/3) */
 } pet_step_rule;
 

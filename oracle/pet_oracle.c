@@ -718,14 +718,17 @@ int o_solve(const og_geom *g, const og_opts *o, const double *m, const double *r
           subset_objective_grad(g, o, i, x, m, rr, y, table + (size_t)i * N, tmp);
           for (size_t v = 0; v < N; v++) G[v] += table[(size_t)i * N + v];
         }
-        /* short BB step from consecutive snapshots (a reading: Sec. 2.2 says BB
-         * values are computed when the full gradient is recomputed) */
+        /* short BB step from consecutive snapshots (Sec. 2.2: computed when the full
+         * gradient is recomputed), taken in the metric of the preconditioner: the
+         * gradient-descent form p'q / q'q applied to the variables D^(-1/2) x, i.e.
+         * p'q / q'Dq.  This reading makes the step dimensionless, on the scale of the
+         * Table 1 caps (3, 2.2, 1) and of the ALG1 steps that also multiply D grad. */
         if (have_snapshot) {
           double pq = 0.0, qq = 0.0;
           for (size_t v = 0; v < N; v++) {
             double pv = x[v] - xhat_old[v], qv = G[v] - G_old[v];
             pq += pv * qv;
-            qq += qv * qv;
+            qq += qv * D[v] * qv;
           }
           if (qq > 0) { tau_bb = pq / qq; have_bb = 1; }
         }

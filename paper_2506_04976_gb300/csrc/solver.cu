@@ -261,17 +261,19 @@ __device__ __forceinline__ double warp_block_sum(double v) {
 }
 
 // BB ingredients at an SVRG refresh, FP64: p = x - xhat_old, q = (G + gS) - Gfull_old;
-// partial sums of p'q and q'q per block; then the snapshot buffers take the new values.
+// partial sums of p'q and q'Dq per block (the short BB step in the metric of the
+// preconditioner D, so that it is on the scale of the other step rules, which also
+// multiply D grad); then the snapshot buffers take the new values.
 __global__ void k_bb_dots(const float *__restrict__ x, float *__restrict__ xhat_old,
                           const float *__restrict__ G, const float *__restrict__ gS,
-                          float *__restrict__ Gfull_old, size_t N, double *part) {
+                          float *__restrict__ Gfull_old, const float *__restrict__ D, size_t N, double *part) {
   double pq = 0.0, qq = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
     const float gf = G[i] + gS[i];
     const double p = (double)x[i] - (double)xhat_old[i];
     const double q = (double)gf - (double)Gfull_old[i];
     pq += p * q;
-    qq += q * q;
+    qq += q * (double)D[i] * q;
     xhat_old[i] = x[i];
     Gfull_old[i] = gf;
   }
@@ -832,7 +834,7 @@ static pet_status iterate(pet_solver *s, long long k, int sub, cudaStream_t st) 
     }
     if (s->xhatT) SCK(cudaMemcpyAsync(s->xhatT, p->d_xT, s->N * 4, cudaMemcpyDeviceToDevice, st));
     note_launch();
-    k_bb_dots<<<ge, 256, 0, st>>>(s->x, s->xhat_old, s->G, s->gS, s->Gfull_old, s->N, s->part);
+    k_bb_dots<<<ge, 256, 0, st>>>(s->x, s->xhat_old, s->G, s->gS, s->Gfull_old, s->D, s->N, s->part);
     note_launch();
     k_bb_final<<<1, 256, 0, st>>>(s->part, (int)ge, s->st);
     note_launch();

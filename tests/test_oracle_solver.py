@@ -151,8 +151,9 @@ def test_svrg_converges_to_kkt_point():
 
 
 def test_bb_step_is_secant_ratio():
-    """Short BB step (Sec. 2.2) at the second SVRG refresh: p^T q / q^T q of the
-    snapshot and full-gradient differences; before that the start value is used."""
+    """Short BB step (Sec. 2.2) at the second SVRG refresh: p^T q / q^T D q of the
+    snapshot and full-gradient differences in the preconditioner's metric (D computed
+    here independently from the start image); before that the start value is used."""
     g = geom2d(8, 12, 8)
     G, xt, m, r, y = _data(g, 6)
     n = 2
@@ -172,8 +173,29 @@ def test_bb_step_is_secant_ratio():
 
     p = snaps[3] - x0  # snapshot at k = 4 is x after iteration 3
     q = full_grad(snaps[3]) - full_grad(x0)
-    assert taus[4] == pytest.approx(float((p * q).sum() / (q * q).sum()), rel=1e-10)
+    _, _, H = O.rdp(x0, (g["dx"], g["dy"], g["dz"]), 2.0, 1e-3)
+    D = O.precond(x0, sens, 0.1 * H, 1.0, 1e-6 * x0.max(), kind=1)
+    assert taus[4] == pytest.approx(float((p * q).sum() / (q * D * q).sum()), rel=1e-10)
     assert np.all(taus[4:8] == taus[4])
+
+
+def test_bb_step_is_dimensionless():
+    """The BB step multiplies D grad, like the Table 1 steps it is capped against: on the
+    2D workload it is of order one, where the ratio p'q / q'q (units of image / gradient)
+    is three orders of magnitude smaller."""
+    p = synth.make_problem("c1", 0)
+    G = O.Geometry(p["geom"])
+    n = p["nsub"]
+    m = O.multiplicative(G, p["mu"].astype(np.float32), p["sens"].astype(np.float32))
+    sens = O.sensitivity(G, 1, -1, m)
+    x = np.ones(G.img_shape)
+    for s in range(n):
+        x = O.em_update(G, n, s, m, p["r"], p["y"], x)
+    niter = 2 * n + 1
+    _, taus, _ = O.solve(G, x, m, p["r"], p["y"], sens, algo=O.SVRG, nsub=n, niter=niter,
+                         order=O.subset_order(1, n, niter), step_rule=O.STEP_BB, tau0=1.0, precond_kind=1,
+                         pc_iters=(0,), beta=p["beta"], gamma=p["gamma"], eps=p["eps"])
+    assert 0.05 < taus[2 * n] < 20.0
 
 
 def test_nrmse_definition():
