@@ -245,11 +245,20 @@ def time_to_nrmse(pet, dev, config, seed=0, threshold=0.01, max_epochs=3000):
     xref = torch.from_numpy(ref["x"]).to(dev)
     mask = torch.from_numpy(p["mask"]).to(dev)
     bg = torch.from_numpy(p["bg"]).to(dev)
-    out = {"reference_kkt": float(ref["kkt"]), "threshold": threshold}
+    # the 2D workload runs the settings it is specified with (SVRG, vanishing steps from
+    # tau0 = 1, eta = 0.02, preconditioner in epochs 1-3); the 3D ones the submitted ALG2
+    from paper_2506_04976_gb300.presets import petric_solver_kwargs
+    if p["geom"]["nz"] == 1:
+        kw = dict(algo=pet.SVRG, omega=2, step_rule=pet.STEP_VANISH, tau0=1.0, eta=0.02, precond_kind=1,
+                  pc_iters=(0, n, 2 * n))
+        method = "SVRG, vanishing steps tau0 = 1, eta = 0.02, harmonic preconditioner in epochs 1-3"
+    else:
+        kw = petric_solver_kwargs("ALG2", n)
+        method = "ALG2 of Table 1 (SVRG, BB steps with caps, harmonic preconditioner in epochs 1, 2, 4, 6)"
+    out = {"reference_kkt": float(ref["kkt"]), "threshold": threshold, "method": method}
     for form in ("graph", "plain"):
-        solver = pet.Solver(plan, algo=pet.SVRG, omega=2, step_rule=pet.STEP_VANISH, tau0=1.0, eta=0.02,
-                            precond_kind=1, pc_iters=(0, n, 2 * n), beta=p["beta"], gamma=p["gamma"],
-                            eps=p["eps"], seed=77, use_graph=(form == "graph"))
+        solver = pet.Solver(plan, beta=p["beta"], gamma=p["gamma"], eps=p["eps"], seed=77,
+                            use_graph=(form == "graph"), **kw)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
