@@ -94,6 +94,18 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+def ncu_instructions(kernel_tag, kernel_name):
+    """Warp instructions per launch of the dominant kernel from the committed ncu summary
+    (same conditions as ncu_traffic); else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    if d.get("source_hash") != source_hash():
+        return None
+    return d.get("warp_instructions_per_launch", {}).get(kernel_name)
+
+
 def ncu_traffic(kernel_tag, kernel_name):
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if
     it profiled the same kernel variant and the kernel source is unchanged since the
@@ -701,6 +713,18 @@ def main():
                 "kernel_ms": kavg, "launches_timed": kern_n, "algorithmic_bytes": abytes,
                 "peak_kind": f"hbm_gbs {peak_kind}", "launch_shape": {"planes_per_thread": shape[0],
                                                                       "parts_per_lor": shape[1]}}
+    # The kernel's working set is L2-resident; what bounds it is instruction issue.  Issue
+    # roofline: 152 SMs x 4 schedulers x 1 warp instruction per cycle at the maximum SM clock.
+    inst = ncu_instructions("k_grad_c2", kname)
+    if inst is not None:
+        sm_max = 2070.0
+        mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(mp):
+            sm_max = float(json.load(open(mp)).get("sm_max_mhz", sm_max))
+        ipeak = 152 * 4 * sm_max * 1e6
+        ach = inst / (kavg * 1e-3)
+        roofline["issue"] = {"achieved": ach, "peak": ipeak, "unit": "warp instructions/s", "frac": ach / ipeak,
+                             "instructions_per_launch": inst, "source": "ncu smsp__inst_executed.sum"}
     cpu = None
     if world == 1 and not args.no_cpu:
         times = cpu_baseline(p, args.cpu_seconds)
