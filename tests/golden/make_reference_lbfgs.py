@@ -15,8 +15,9 @@ recorded and the image saved (float32) to tests/golden/ref_<config>_seed<k>.npz.
     python tests/golden/make_reference_lbfgs.py c2 0 [--workers 7] [--maxiter 600]
         [--init file.npz] [--out file.npz]
 
---init restarts from an image this script wrote (the KKT normalisation always refers to
-the OSEM start image and is stored with the result as g0_norm); --out writes elsewhere
+--init restarts from an image this script wrote, with the variable scaling recomputed
+there (the KKT normalisation always refers to the OSEM start image and is stored with
+the result as g0_norm); --out writes elsewhere
 than tests/golden, e.g. while the run is still far from converged.
 """
 import argparse
@@ -75,8 +76,9 @@ def main():
     for s in range(n):  # one OSEM epoch (Sec. 3.1)
         x = O.em_update(G, n, s, m, p["r"], p["y"], x)
     sens = O.sensitivity(G, 1, -1, m)
-    _, _, H = O.rdp(x, sp, p["gamma"], p["eps"])
-    D = O.precond(x, sens, beta * H, 1.0, 1e-6 * x.max(), kind=1)
+    xs = np.load(a.init)["x"].astype(np.float64) if a.init else x  # scaling from the start image
+    _, _, H = O.rdp(xs, sp, p["gamma"], p["eps"])
+    D = O.precond(xs, sens, beta * H, 1.0, 1e-6 * xs.max(), kind=1)
     d = np.sqrt(np.maximum(D, 1e-12 * D.max()))
 
     ctx = mp.get_context("spawn")
