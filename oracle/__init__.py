@@ -60,7 +60,7 @@ class _Opts(C.Structure):
         ("kappa", C.POINTER(C.c_double)),
         ("order", C.POINTER(C.c_int)),
         ("sampling", C.c_int), ("sample_seed", C.c_uint64),
-        ("subsets_out", C.POINTER(C.c_int)),
+        ("subsets_out", C.POINTER(C.c_int)), ("bb_until", C.c_long),
     ]
 
 
@@ -283,11 +283,12 @@ def step_alg2(k, nsub, tau_bb):
 def solve(G: Geometry, x0, m, r, y, sens, *, algo, nsub, niter, order, omega=2,
           step_rule=STEP_VANISH, tau0=1.0, eta=0.02, precond_kind=1, alpha=1.0,
           delta_rel=1e-6, pc_iters=(0,), beta=0.1, gamma=2.0, eps=1e-3, kappa=None,
-          snap_every=0, sampling=SAMPLE_PERM, sample_seed=0, subsets_out=None):
+          snap_every=0, sampling=SAMPLE_PERM, sample_seed=0, subsets_out=None, bb_until=0):
     """Runs SGD/SAGA/SVRG (eq. 6-9, Algorithm 1) from x0; returns (x, taus, snaps).
     With sampling=SAMPLE_IMPORTANCE (SVRG) the subsets are drawn inside from
     sample_seed and `order` is ignored; subsets_out (int32 array of length niter, may
-    be None) receives the subset of every iteration (-1 at snapshot refreshes)."""
+    be None) receives the subset of every iteration (-1 at snapshot refreshes).  bb_until
+    > 0 recomputes the BB step only at refreshes k <= bb_until (Table 1: epochs 2, 4, 6)."""
     x = _f64(x0).copy()
     m, r, y, sens = _f64(m), _f64(r), _f64(y), _f64(sens)
     order = np.ascontiguousarray(order, np.int32)
@@ -296,7 +297,7 @@ def solve(G: Geometry, x0, m, r, y, sens, *, algo, nsub, niter, order, omega=2,
     o = _Opts(algo, nsub, niter, omega, step_rule, tau0, eta, precond_kind, alpha, delta_rel,
               pcs.ctypes.data_as(C.POINTER(C.c_long)), len(pcs), beta, gamma, eps,
               _d(kap) if kap is not None else None, _i(order), sampling, C.c_uint64(sample_seed),
-              _i(subsets_out) if subsets_out is not None else None)
+              _i(subsets_out) if subsets_out is not None else None, C.c_long(bb_until))
     taus = np.zeros(niter)
     nsnap = niter // snap_every if snap_every > 0 else 0
     snaps = np.zeros((max(nsnap, 1),) + x.shape)

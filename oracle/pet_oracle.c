@@ -633,6 +633,8 @@ typedef struct {
   int sampling;                    /* O_SAMPLE_IMPORTANCE draws inside (SVRG); else order */
   uint64_t sample_seed;            /* importance draws: u_k from o_splitmix64_at(seed, k) */
   int *subsets_out;                /* may be NULL: subset used by each non-refresh iteration */
+  long bb_until;                   /* BB step recomputed only at refreshes k <= bb_until
+                                      (0: at every refresh); later it stays fixed */
 } og_opts;
 
 /* Gradient of f_i at x: data gradient of subset i plus (beta/n) grad S. */
@@ -723,7 +725,7 @@ int o_solve(const og_geom *g, const og_opts *o, const double *m, const double *r
          * gradient-descent form p'q / q'q applied to the variables D^(-1/2) x, i.e.
          * p'q / q'Dq.  This reading makes the step dimensionless, on the scale of the
          * Table 1 caps (3, 2.2, 1) and of the ALG1 steps that also multiply D grad. */
-        if (have_snapshot) {
+        if (have_snapshot && (o->bb_until <= 0 || k <= o->bb_until)) {
           double pq = 0.0, qq = 0.0;
           for (size_t v = 0; v < N; v++) {
             double pv = x[v] - xhat_old[v], qv = G[v] - G_old[v];

@@ -242,3 +242,22 @@ def test_variance_reduced_estimators_vanish_at_the_minimiser():
         moved[algo] = np.linalg.norm(x - xs) / np.linalg.norm(xs)
     assert moved[O.SVRG] < 1e-5 and moved[O.SAGA] < 1e-5  # ~7e-8: the reference's own residual
     assert moved[O.SGD] > 1e-2
+
+
+def test_bb_step_frozen_after_bb_until():
+    """Table 1 computes the BB step of ALG2/ALG3 at the ends of epochs 2, 4 and 6 only:
+    with bb_until the step of later refreshes keeps the last value, while without it a
+    new secant ratio is taken at every refresh."""
+    g = geom2d(8, 12, 8)
+    G, xt, m, r, y = _data(g, 6)
+    n = 2
+    sens = O.sensitivity(G, 1, -1, m)
+    x0 = np.ones(G.img_shape)
+    niter = 13
+    kw = dict(algo=O.SVRG, nsub=n, niter=niter, order=O.subset_order(3, n, niter), tau0=0.5, precond_kind=1,
+              beta=0.1, pc_iters=(0,), omega=2, step_rule=O.STEP_BB)
+    _, t_all, _ = O.solve(G, x0, m, r, y, sens, **kw)
+    _, t_frz, _ = O.solve(G, x0, m, r, y, sens, bb_until=4, **kw)
+    assert np.array_equal(t_all[:8], t_frz[:8])          # refreshes at k = 0, 4 are the same
+    assert np.all(t_frz[8:] == t_frz[4])                  # k = 8, 12: frozen at the k = 4 value
+    assert t_all[8] != t_all[4] and t_all[12] != t_all[8]  # recomputed without the limit
