@@ -252,6 +252,8 @@ typedef struct {
                              recomputes the subset gradient at the snapshot (two fused
                              gradients per iteration); the refresh computes the full data
                              gradient in one pass over all views */
+  long long bb_until;     /* BB step recomputed only at refreshes k <= bb_until, then kept
+                             (Table 1: ends of epochs 2, 4, 6 for ALG2/ALG3); 0 = every refresh */
 } pet_solver_opts;
 
 pet_status pet_solver_create(pet_plan *plan, const pet_solver_opts *opts, pet_solver **out);

@@ -74,7 +74,7 @@ class SolverOpts(C.Structure):
         ("seed", C.c_ulonglong),
         ("order", C.POINTER(C.c_int)), ("norder", C.c_longlong),
         ("use_graph", C.c_int), ("deterministic", C.c_int),
-        ("sampling", C.c_int), ("low_memory", C.c_int),
+        ("sampling", C.c_int), ("low_memory", C.c_int), ("bb_until", C.c_longlong),
     ]
 
 
@@ -325,7 +325,7 @@ class Solver:
     def __init__(self, plan: Plan, *, algo=SVRG, omega=2, step_rule=STEP_VANISH, tau0=1.0, eta=0.02,
                  precond_kind=1, alpha=1.0, delta_rel=1e-6, pc_iters=(0,), beta=0.1, gamma=2.0,
                  eps=1e-3, kappa=None, seed=0, order=None, use_graph=True, deterministic=False,
-                 sampling=SAMPLE_PERM, low_memory=False):
+                 sampling=SAMPLE_PERM, low_memory=False, bb_until=0):
         self.plan = plan
         self._pc = np.ascontiguousarray(pc_iters, np.int64)
         self._order = np.ascontiguousarray(order, np.int32) if order is not None else None
@@ -336,7 +336,8 @@ class Solver:
                        seed,
                        self._order.ctypes.data_as(C.POINTER(C.c_int)) if self._order is not None else None,
                        len(self._order) if self._order is not None else 0,
-                       int(bool(use_graph)), int(bool(deterministic)), int(sampling), int(bool(low_memory)))
+                       int(bool(use_graph)), int(bool(deterministic)), int(sampling), int(bool(low_memory)),
+                       int(bb_until))
         h = _vp()
         _ck(_lib.pet_solver_create(plan._h, C.byref(o), C.byref(h)), "pet_solver_create")
         self._h = h

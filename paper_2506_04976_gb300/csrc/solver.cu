@@ -283,7 +283,7 @@ __global__ void k_bb_dots(const float *__restrict__ x, float *__restrict__ xhat_
   if (threadIdx.x == 0) part[2 * blockIdx.x + 1] = b;
 }
 
-__global__ void k_bb_final(const double *part, int nb, SolverState *st) {
+__global__ void k_bb_final(const double *part, int nb, SolverState *st, int update) {
   double pq = 0.0, qq = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) { pq += part[2 * b]; qq += part[2 * b + 1]; }
   pq = warp_block_sum(pq);
@@ -291,7 +291,7 @@ __global__ void k_bb_final(const double *part, int nb, SolverState *st) {
   if (threadIdx.x != 0) return;
   st->dots[0] = pq;
   st->dots[1] = qq;
-  if (st->have_snapshot && qq > 0.0) {
+  if (update && st->have_snapshot && qq > 0.0) {
     st->tau_bb = pq / qq;
     st->have_bb = 1;
   }
@@ -836,7 +836,7 @@ static pet_status iterate(pet_solver *s, long long k, int sub, cudaStream_t st) 
     note_launch();
     k_bb_dots<<<ge, 256, 0, st>>>(s->x, s->xhat_old, s->G, s->gS, s->Gfull_old, s->D, s->N, s->part);
     note_launch();
-    k_bb_final<<<1, 256, 0, st>>>(s->part, (int)ge, s->st);
+    k_bb_final<<<1, 256, 0, st>>>(s->part, (int)ge, s->st, s->o.bb_until <= 0 || k <= s->o.bb_until ? 1 : 0);
     note_launch();
     k_update<3><<<tile_grid(s), dim3(32, 8), 0, st>>>(upd_args(s, -1, k));
   } else {

@@ -32,12 +32,15 @@ def petric_solver_kwargs(name: str, nsubsets: int) -> dict:
     two epochs), harmonic preconditioner updated at the start of the listed epochs
     (epoch e starts at iteration (e - 1) n), the ALG1 piecewise steps or the BB steps
     capped as in ALG2/ALG3, subsets without replacement (ALG1, ALG2) or in cofactor order
-    (ALG3).  The BB step is recomputed at every snapshot refresh (every two epochs), not
-    only at the end of epochs 2, 4 and 6 as Table 1 lists."""
+    (ALG3).  The BB step is computed at the snapshot refreshes that end epochs 2, 4 and 6
+    and kept afterwards; before the first one the caps themselves are the steps (tau0 = 3
+    is above every cap)."""
     if name not in _TARGET:
         raise ValueError(f"unknown algorithm {name!r} (ALG1, ALG2 or ALG3)")
     n = int(nsubsets)
+    alg1 = name == "ALG1"
     return dict(algo=pet.SVRG, omega=2, precond_kind=1, alpha=1.0,
                 pc_iters=tuple((e - 1) * n for e in _PC_EPOCHS[name]),
-                step_rule=pet.STEP_ALG1 if name == "ALG1" else pet.STEP_ALG2, tau0=1.0,
+                step_rule=pet.STEP_ALG1 if alg1 else pet.STEP_ALG2, tau0=1.0 if alg1 else 3.0,
+                bb_until=0 if alg1 else 6 * n,
                 sampling=pet.SAMPLE_COFACTOR if name == "ALG3" else pet.SAMPLE_PERM)

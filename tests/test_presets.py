@@ -33,5 +33,7 @@ def test_solver_settings():
     assert a1["step_rule"] == pet.STEP_ALG1 and a2["step_rule"] == a3["step_rule"] == pet.STEP_ALG2
     assert a1["sampling"] == a2["sampling"] == pet.SAMPLE_PERM and a3["sampling"] == pet.SAMPLE_COFACTOR
     assert all(a["algo"] == pet.SVRG and a["precond_kind"] == 1 for a in (a1, a2, a3))
+    assert a1["bb_until"] == 0 and a2["bb_until"] == a3["bb_until"] == 6 * n
+    assert a2["tau0"] >= 3.0  # before the first BB step the Table 1 caps apply
     with pytest.raises(ValueError):
         presets.petric_solver_kwargs("ALG4", n)
