@@ -2,7 +2,7 @@
 by the committed scripts beside them from the oracle alone) satisfy the optimality
 conditions of min_x D(x) + beta S(x), x >= 0 (eq. 1 with the prior of eq. 3): the KKT
 residual ||min(x, grad F(x))|| / ||grad F(x_osem)||, recomputed here with the oracle
-from the image as stored (float32), is below 1e-5, and the image is nonnegative.  The
+from the image as stored (float32), is below 1e-6, and the image is nonnegative.  The
 normalisation ||grad F(x_osem)|| is recomputed for the 2D image and taken from the file
 (written there by the oracle-only script) for the 3D ones, whose OSEM epoch takes long."""
 import os
@@ -50,4 +50,4 @@ def test_reference_is_a_kkt_point(cfg, seed):
             x0 = O.em_update(G, n, s, m, p["r"], p["y"], x0)
         g0n = np.linalg.norm(grad(x0))
     res = np.linalg.norm(np.minimum(x, grad(x))) / g0n
-    assert res < 1e-5, res
+    assert res < 1e-6, res
