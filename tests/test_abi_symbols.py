@@ -39,3 +39,18 @@ def test_status_strings():
     lib.pet_status_str.restype = ctypes.c_char_p
     assert lib.pet_status_str(0) == b"ok"
     assert b"infeasible" in lib.pet_status_str(3)
+
+
+def test_binding_refuses_to_load_without_the_library(tmp_path):
+    """A copy of the binding whose library directory is empty raises ImportError at
+    import: no operation can fall back to the CPU."""
+    import importlib.util
+    src = os.path.join(ROOT, "paper_2506_04976_gb300", "binding.py")
+    pkg = tmp_path / "pkg_without_lib"
+    pkg.mkdir()
+    dst = pkg / "binding.py"
+    dst.write_text(open(src).read())
+    spec = importlib.util.spec_from_file_location("binding_without_lib", str(dst))
+    mod = importlib.util.module_from_spec(spec)
+    with pytest.raises(ImportError, match="is missing"):
+        spec.loader.exec_module(mod)
