@@ -52,7 +52,7 @@ def parse():
                     help="grad mode: 'auto' (autotuner) or 'K,S' planes per thread, parts per LOR")
     ap.add_argument("--config", default="c2", choices=["c2", "c3"],
                     help="grad mode: c2 (non-TOF, 1e7 counts) or c3 (11 TOF bins, 1e6 counts)")
-    ap.add_argument("--study-config", default="c1", choices=["c1", "c2", "c2s", "c2s16"],
+    ap.add_argument("--study-config", default="c1", choices=["c1", "c2", "c2s", "c2s16", "c3s"],
                     help="study mode: workload with a converged reference image in tests/golden")
     return ap.parse_args()
 
@@ -368,9 +368,10 @@ def run_configs(args, pet, dev):
 
 def run_study(args, pet, dev, max_epochs=1500):
     """The comparison of Sec. 3.2 (Fig. 2) against a converged oracle image (2D workload by
-    default, 3D with --study-config c2): SGD / SAGA / SVRG x MLEM / harmonic preconditioner
-    x tau0 in {0.3, 1, 1.5}, vanishing steps (eta = 0.02), preconditioner updated in epochs
-    1-3, subsets without replacement; then the three submitted algorithms (Table 1).
+    default, 3D with --study-config c2 / c2s / c2s16, 3D TOF with c3s): SGD / SAGA / SVRG
+    x MLEM / harmonic preconditioner x tau0 in {0.3, 1, 1.5}, vanishing steps (eta = 0.02),
+    preconditioner updated in epochs 1-3, subsets without replacement; then the three
+    submitted algorithms (Table 1).
     Epochs and GPU seconds from the OSEM start to NRMSE < 1%, and the NRMSE after
     5 ... 500 epochs."""
     import torch
@@ -735,7 +736,7 @@ def main():
     clocks = clk.summary()
     nrmse_times = {}
     if not args.no_nrmse:
-        for cfg in ("c1", "c2", "c2s"):
+        for cfg in ("c1", "c2", "c2s", "c3s"):
             t = time_to_nrmse(pet, dev, cfg)
             if t is not None:
                 nrmse_times[cfg] = t
