@@ -220,6 +220,20 @@ def test_generated_problem_counts_and_shapes():
     assert len(z1) == 1293 and np.abs(z1 - z2).max() <= 34 * 4.0 + 1e-9
 
 
+def test_study_workloads_are_half_resolution_versions():
+    """c2s / c2s16 / c3s keep c2's and c3's physics at half the sizes; only c2s16 changes
+    the prior strength (16 instead of 4 at 1e7 counts), only c3s carries TOF bins."""
+    for name, T, beta in (("c2s", 1, 4 * 2e-4 * 1e7 / 3e7), ("c2s16", 1, 16 * 2e-4 * 1e7 / 3e7),
+                          ("c3s", 11, 4 * 2e-4 * 1e6 / 3e7)):
+        prm = synth._setup(name, 0)
+        g = prm["geom"]
+        assert (g["nx"], g["ny"], g["nz"], g["nrad"], g["nview"], g["ntof"]) == (64, 64, 23, 125, 84, T)
+        assert len(g["z1"]) == 23 + 2 * (23 - 16) and prm["nsub"] == 21
+        assert abs(prm["beta"] - beta) <= 1e-12 * beta
+        assert abs(g["dx"] - 4.0) < 1e-12 and abs(g["drad"] - 4.0) < 1e-12
+    assert synth._setup("c3s", 0)["geom"]["tof_bin"] == synth._setup("c3", 0)["geom"]["tof_bin"] == 33.0
+
+
 def test_variance_reduced_estimators_vanish_at_the_minimiser():
     """At the converged image x* (the stored 2D reference, KKT residual ~1e-7) the SVRG and
     SAGA estimators equal grad J(x*), which is ~0 on the support: their iterates stay at x*
