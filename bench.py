@@ -259,8 +259,9 @@ def time_to_nrmse(pet, dev, config, seed=0, threshold=0.01, max_epochs=3000):
     bg = torch.from_numpy(p["bg"]).to(dev)
     # the 2D workload runs the settings it is specified with (SVRG, vanishing steps from
     # tau0 = 1, eta = 0.02, preconditioner in epochs 1-3); the 3D ones the submitted ALG1
-    # (its piecewise steps keep converging on them; the BB steps of ALG2/ALG3, frozen after
-    # epoch 6 as Table 1 has it, stall on the full-size 3D workload)
+    # (its steps end at 0.5 and keep converging on them; ALG2/ALG3 keep a step of 0.7-1
+    # after epoch 6, the BB value or its cap in Table 1, and stall on the full-size 3D
+    # workload)
     from paper_2506_04976_gb300.presets import petric_solver_kwargs
     if p["geom"]["nz"] == 1:
         kw = dict(algo=pet.SVRG, omega=2, step_rule=pet.STEP_VANISH, tau0=1.0, eta=0.02, precond_kind=1,
