@@ -165,7 +165,11 @@ pet_status pet_em_update(pet_plan *plan, int subset, float *x, void *stream);
 
 /* RDP gradient, Hessian diagonal and value (eq. 3, Appendix A.1), each scaled by
  * p->scale: grad = scale dS/dx, hdiag = scale d2S/dx2, val = scale S (FP64).  Any of
- * grad, hdiag, val may be NULL.  accumulate != 0 adds into grad instead of writing. */
+ * grad, hdiag, val may be NULL.  accumulate is a bit set: PET_RDP_ACC_GRAD adds into
+ * grad instead of writing it; PET_RDP_ACC_VAL adds scale S to *val instead of writing
+ * it (e.g. onto the KL value of pet_ratio, giving the subset objective of eq. 5). */
+#define PET_RDP_ACC_GRAD 1
+#define PET_RDP_ACC_VAL 2
 pet_status pet_rdp(const pet_rdp_params *p, const float *x, float *grad, float *hdiag,
                    double *val, int accumulate, void *stream);
 
@@ -179,9 +183,12 @@ pet_status pet_rdp(const pet_rdp_params *p, const float *x, float *grad, float *
  *   - Images needing more than PET_RDP_STATIC_MAX_PARTIALS stencil blocks of 32x8x4
  *     voxels (more than about 67 million voxels) are rejected with
  *     PET_ERR_UNSUPPORTED when val is requested.
- *   - The first call on a device (with val != NULL) looks up the array's device
- *     address with that device current; make that first call before any stream
- *     capture.  Later calls only reuse the cached address.
+ *   - A call with val != NULL on a stream that is not being captured looks up the
+ *     array's device address on the current device (so an address cached before a
+ *     cudaDeviceReset is never reused); a call on a capturing stream reuses the address
+ *     cached by an earlier call on that device and fails with PET_ERR_STATE if there
+ *     was none.  So make the first call on each device before any stream capture, and
+ *     after a cudaDeviceReset call once outside capture before capturing again.
  *   - All calls share the one array, which keeps the last call's contents.  Calls
  *     that overlap on the GPU (different streams without ordering) race on it. */
 #define PET_RDP_STATIC_MAX_PARTIALS 65536

@@ -35,10 +35,9 @@ class SubsetObjective(torch.autograd.Function):
         elif mode == "store":
             ax = plan.forward(xd, subset)
             obj, _ = plan.ratio(ax, subset, want_q=False)
-            if prior is not None:
-                v, _, _ = pet.rdp(xd, plan.spacing, prior[1], prior[2], prior[0],
-                                  prior[3] if len(prior) > 3 else None, want_grad=False, want_hdiag=False)
-                obj = obj + v
+            if prior is not None:  # the library adds (beta/n) S(x) onto the KL value
+                pet.rdp(xd, plan.spacing, prior[1], prior[2], prior[0], prior[3] if len(prior) > 3 else None,
+                        want_grad=False, want_hdiag=False, val_out=obj, accumulate_val=True)
             ctx.save_for_backward(xd, ax)
         else:
             raise ValueError(mode)

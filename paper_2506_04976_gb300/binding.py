@@ -299,16 +299,23 @@ def _wrap(ptr, shape):
     return torch.as_tensor(_Iface(), device="cuda")
 
 
+RDP_ACC_GRAD, RDP_ACC_VAL = 1, 2
+
+
 def rdp(x, spacing, gamma, eps, scale=1.0, kappa=None, want_grad=True, want_hdiag=True,
-        want_val=True, grad_out=None, accumulate=False):
-    """(scale*S(x), scale*grad S, scale*diag Hess S) of eq. 3 on the GPU."""
+        want_val=True, grad_out=None, accumulate=False, val_out=None, accumulate_val=False):
+    """(scale*S(x), scale*grad S, scale*diag Hess S) of eq. 3 on the GPU.  accumulate adds
+    the gradient into grad_out; accumulate_val adds scale*S into val_out (a 0-d float64
+    CUDA tensor) instead of overwriting it."""
     g = (torch.empty_like(x) if grad_out is None else grad_out) if want_grad else None
     h = torch.empty_like(x) if want_hdiag else None
-    v = torch.zeros((), device=x.device, dtype=torch.float64) if want_val else None
+    v = (torch.zeros((), device=x.device, dtype=torch.float64) if val_out is None else val_out) \
+        if want_val else None
     p = rdp_params(tuple(x.shape), spacing, gamma, eps, scale, kappa)
+    flags = (RDP_ACC_GRAD if accumulate else 0) | (RDP_ACC_VAL if accumulate_val else 0)
     _ck(_lib.pet_rdp(C.byref(p), _ptr(x), _ptr(g) if g is not None else None,
                      _ptr(h) if h is not None else None, _ptr(v, torch.float64) if v is not None else None,
-                     int(accumulate), _stream()), "pet_rdp")
+                     flags, _stream()), "pet_rdp")
     return v, g, h
 
 

@@ -427,8 +427,8 @@ extern "C" pet_status pet_rdp(const pet_rdp_params *p, const float *x, float *gr
   double *part = nullptr;
   const int nb = rdp_blocks(p->nx, p->ny, p->nz);
   if (val && cudaMallocAsync((void **)&part, nb * sizeof(double), st) != cudaSuccess) return PET_ERR_NOMEM;
-  cudaError_t e = launch_rdp(a, x, grad, hdiag, part, accumulate, nullptr, st);
-  if (e == cudaSuccess && val) e = launch_reduce_sum(part, nb, val, 0, st);
+  cudaError_t e = launch_rdp(a, x, grad, hdiag, part, accumulate & PET_RDP_ACC_GRAD, nullptr, st);
+  if (e == cudaSuccess && val) e = launch_reduce_sum(part, nb, val, (accumulate & PET_RDP_ACC_VAL) ? 1 : 0, st);
   if (part) cudaFreeAsync(part, st);
   return e == cudaSuccess ? PET_OK : PET_ERR_CUDA;
 }

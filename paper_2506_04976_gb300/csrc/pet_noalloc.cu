@@ -24,17 +24,24 @@ void *g_partials_addr[kMaxDevices] = {nullptr};
 std::mutex g_mu;
 
 // Device address of g_rdp_partials on the current device.  In host code the array's
-// name only stands for the symbol; its device address comes from the runtime, once per
-// device, with that device current.
-pet_status partials_address(double **out) {
+// name only stands for the symbol; its device address comes from the runtime, looked up
+// with the device current.  Outside stream capture the lookup is repeated on every call,
+// so an address cached before a cudaDeviceReset (which unloads the module) is never
+// used again; under capture (where a lookup could trigger module loading) the address
+// cached by the last call outside capture on this device is used.
+pet_status partials_address(cudaStream_t st, double **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return PET_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return PET_ERR_UNSUPPORTED;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return PET_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_partials_addr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_rdp_partials) != cudaSuccess || !p) return PET_ERR_CUDA;
     g_partials_addr[dev] = p;
+  } else if (!g_partials_addr[dev]) {
+    return PET_ERR_STATE;
   }
   *out = static_cast<double *>(g_partials_addr[dev]);
   return PET_OK;
@@ -46,17 +53,17 @@ extern "C" pet_status pet_rdp_static(const pet_rdp_params *p, const float *x, fl
                                      double *val, int accumulate, void *stream) {
   if (!p || !x || p->nx < 1 || p->ny < 1 || p->nz < 1) return PET_ERR_ARG;
   const int nb = rdp_blocks(p->nx, p->ny, p->nz);
+  cudaStream_t s = (cudaStream_t)stream;
   double *part = nullptr;
   if (val) {
     if (nb > PET_RDP_STATIC_MAX_PARTIALS) return PET_ERR_UNSUPPORTED;
-    const pet_status st = partials_address(&part);
+    const pet_status st = partials_address(s, &part);
     if (st != PET_OK) return st;
   }
   // Every partial that the reduction reads is written by this call's stencil launch, so
   // nothing in the shared array has to be cleared first.
-  cudaStream_t s = (cudaStream_t)stream;
   const RdpArgs a = make_rdp_args(*p);
-  cudaError_t e = launch_rdp(a, x, grad, hdiag, part, accumulate, nullptr, s);
-  if (e == cudaSuccess && val) e = launch_reduce_sum(part, nb, val, 0, s);
+  cudaError_t e = launch_rdp(a, x, grad, hdiag, part, accumulate & PET_RDP_ACC_GRAD, nullptr, s);
+  if (e == cudaSuccess && val) e = launch_reduce_sum(part, nb, val, (accumulate & PET_RDP_ACC_VAL) ? 1 : 0, s);
   return e == cudaSuccess ? PET_OK : PET_ERR_CUDA;
 }

@@ -100,6 +100,47 @@ def test_n1_svrg_saga_sgd_equal_projected_gd():
         assert np.allclose(xa, x, rtol=1e-11, atol=1e-13)
 
 
+def test_vanishing_step_rule_hand_values():
+    """Sec. 2.2's vanishing rule tau_k = tau0 / (1 + eta k / n), k the 0-based update
+    index over all epochs: hand-computed values at n = 6, eta = 0.02, tau0 = 1.5 (k
+    instead of k/n, k + 1 instead of k, or a dropped tau0 each fail one of them)."""
+    g = geom2d(8, 12, 12)
+    G, xt, m, r, y = _data(g, 6)
+    sens = O.sensitivity(G, 1, -1, m)
+    n, niter = 6, 601
+    _, taus, _ = O.solve(G, np.full(G.img_shape, 1.0), m, r, y, sens, algo=O.SGD, nsub=n, niter=niter,
+                         order=O.subset_order(5, n, niter), step_rule=O.STEP_VANISH, tau0=1.5, eta=0.02,
+                         precond_kind=0, beta=0.0, pc_iters=(0,))
+    hand = {0: 1.5, 5: 1.4754098360655739, 6: 1.4705882352941176, 12: 1.4423076923076923, 600: 0.5}
+    for k, v in hand.items():
+        assert taus[k] == pytest.approx(v, rel=1e-15), k
+
+
+def test_vanishing_step_drives_the_updates():
+    """The recorded vanishing steps are the ones the iterates use: three SGD updates
+    (n = 2, eta = 0.4, tau0 = 1.5: steps 1.5, 1.25, 1.5/1.4 by hand) composed from the
+    pinned data gradient, RDP and preconditioner parts."""
+    g = geom2d(8, 12, 12)
+    G, xt, m, r, y = _data(g, 7)
+    n, beta = 2, 0.05
+    sp = (g["dx"], g["dy"], g["dz"])
+    sens = O.sensitivity(G, 1, -1, m)
+    order = np.array([1, 0, 0], np.int32)
+    x0 = np.full(G.img_shape, 1.0)
+    xs, taus, _ = O.solve(G, x0, m, r, y, sens, algo=O.SGD, nsub=n, niter=3, order=order,
+                          step_rule=O.STEP_VANISH, tau0=1.5, eta=0.4, precond_kind=0, beta=beta,
+                          pc_iters=(0,))
+    steps = (1.5, 1.25, 1.0714285714285714)
+    assert np.allclose(taus, steps, rtol=1e-15)
+    x = x0.copy()
+    D = O.precond(x, sens, None, 1.0, 1e-6 * x.max(), kind=0)
+    for k, i in enumerate(order):
+        _, gd = O.data_grad(G, n, int(i), x, m, r, y)
+        _, gs, _ = O.rdp(x, sp, 2.0, 1e-3)
+        x = np.maximum(0.0, x - steps[k] * D * (n * gd + beta * gs))
+    assert np.allclose(xs, x, rtol=1e-11, atol=1e-13)
+
+
 @pytest.mark.parametrize("algo", [O.SGD, O.SAGA, O.SVRG])
 def test_estimators_unbiased_second_iteration(algo):
     """With no clipping by the prox, averaging iteration 2 over the subset drawn equals
