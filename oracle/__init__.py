@@ -74,6 +74,7 @@ def lib():
         _lib.o_kl_term.restype = C.c_double
         _lib.o_tof_weight.restype = C.c_double
         _lib.o_data_grad.restype = C.c_double
+        _lib.o_data_grad_views.restype = C.c_double
         _lib.o_rdp.restype = C.c_double
         _lib.o_nrmse.restype = C.c_double
         _lib.o_step_alg1.restype = C.c_double
@@ -209,6 +210,22 @@ def data_grad(G: Geometry, nsub, s, x, m, r, y, want_grad=True):
     x, m, r, y = _f64(x), _f64(m), _f64(r), _f64(y)
     g = np.zeros(G.img_shape) if want_grad else None
     val = lib().o_data_grad(G.ref, nsub, s, _d(x), _d(m), _d(r), _d(y), _d(g) if want_grad else None)
+    return val, g
+
+
+def data_grad_views(G: Geometry, views, x, m_c, r_c, y_c, want_grad=True):
+    """(D(x), grad D(x)) over the listed views with compact data: m_c (nv, P, R), r_c and
+    y_c (nv, P, R, T) for those views in order (P, R, T of G's plane list)."""
+    views = np.ascontiguousarray(views, np.int32)
+    x, m_c, r_c, y_c = _f64(x), _f64(m_c), _f64(r_c), _f64(y_c)
+    nv = len(views)
+    if m_c.size != nv * G.s.nplane * G.s.nrad or r_c.size != m_c.size * G.T or y_c.size != r_c.size:
+        raise ValueError("compact data do not match the views and the geometry")
+    g = np.zeros(G.img_shape) if want_grad else None
+    val = lib().o_data_grad_views(G.ref, _i(views), nv, _d(x), _d(m_c), _d(r_c), _d(y_c),
+                                  _d(g) if want_grad else None)
+    if not np.isfinite(val) and np.all(np.isfinite(r_c)):
+        raise ValueError("axial axis would drive a LOR, or infeasible data")
     return val, g
 
 

@@ -370,6 +370,33 @@ double o_data_grad(const og_geom *g, int nsub, int s, const double *x, const dou
   return val;
 }
 
+/* The same data term and gradient (eq. 5, KL of Sec. 1.2) over an explicit list of
+ * views whose data are given in compact layout: m_c [j][P][R], r_c and y_c
+ * [j][P][R][T] for j over the listed views.  With the plane list of g restricted to a
+ * subset of the scanner's planes this evaluates the share of those LORs, so a large
+ * subset can be split into pieces whose values and gradients add up.  grad (may be
+ * NULL) is overwritten.  Returns the data term value, or NAN if a LOR cannot be
+ * represented (axial driving axis). */
+double o_data_grad_views(const og_geom *g, const int *views, int nv, const double *x, const double *m_c,
+                         const double *r_c, const double *y_c, double *grad) {
+  int T = g->ntof > 1 ? g->ntof : 1;
+  size_t nl = (size_t)nv * g->nplane * g->nrad;
+  double *px = malloc(sizeof(double) * nl * T);
+  double *q = malloc(sizeof(double) * nl * T);
+  int rc = o_project(g, views, nv, x, px);
+  double val = 0.0;
+  for (size_t l = 0; l < nl; l++)
+    for (int b = 0; b < T; b++) {
+      double ybar = m_c[l] * px[l * T + b] + r_c[l * T + b];
+      double yy = y_c[l * T + b];
+      val += o_kl_term(ybar, yy);
+      q[l * T + b] = m_c[l] * (1.0 - yy / ybar);
+    }
+  if (grad && o_backproject(g, views, nv, q, grad) != 0) rc = -1;
+  free(px); free(q);
+  return rc == 0 ? val : NAN;
+}
+
 /* Sensitivity A_s^T 1 (all TOF bins) for subset s (s=-1: all views). */
 void o_sensitivity(const og_geom *g, int nsub, int s, const double *m, double *sens_img) {
   int T = g->ntof > 1 ? g->ntof : 1;

@@ -69,6 +69,42 @@ def test_subsets_partition_the_data_term():
     assert np.allclose(sum(p[1] for p in parts), gfull, rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("tof", [1, 5])
+def test_compact_view_pieces_add_up_to_the_subset_data_term(tof):
+    """The compact-data form over pieces (one view and a run of planes each) adds up to the
+    subset's data term and gradient (eq. 5), and its gradient matches central finite
+    differences of its own value."""
+    g = geom3d(6, 3, 9, 6, ntof=tof, tof_sigma=6.0, tof_bin=8.0)
+    G, x, m, r, y = _problem(g, 5)
+    nsub, s = 2, 1
+    val, grad = O.data_grad(G, nsub, s, x, m, r, y)
+    P = len(g["z1"])
+    tot, gsum = 0.0, np.zeros_like(grad)
+    for v in O.subset_views(g["nview"], nsub, s):
+        for p0, p1 in ((0, 2), (2, P)):
+            gk = dict(g, z1=g["z1"][p0:p1], z2=g["z2"][p0:p1])
+            vk, gr = O.data_grad_views(O.Geometry(gk), [v], x, m[v:v + 1, p0:p1], r[v:v + 1, p0:p1],
+                                       y[v:v + 1, p0:p1])
+            tot += vk
+            gsum += gr
+    assert abs(tot - val) <= 1e-12 * abs(val)
+    assert np.allclose(gsum, grad, rtol=1e-12, atol=1e-12 * np.abs(grad).max())
+    Gk = O.Geometry(dict(g, z1=g["z1"][1:3], z2=g["z2"][1:3]))
+    v = 2
+    args = (m[v:v + 1, 1:3], r[v:v + 1, 1:3], y[v:v + 1, 1:3])
+    _, gk = O.data_grad_views(Gk, [v], x, *args)
+    rng = np.random.default_rng(2)
+    for idx in rng.integers(0, x.size, 8):
+        h = 1e-5
+        xp, xm = x.copy().ravel(), x.copy().ravel()
+        xp[idx] += h
+        xm[idx] -= h
+        fp, _ = O.data_grad_views(Gk, [v], xp.reshape(x.shape), *args, want_grad=False)
+        fm, _ = O.data_grad_views(Gk, [v], xm.reshape(x.shape), *args, want_grad=False)
+        fd = (fp - fm) / (2 * h)
+        assert abs(fd - gk.ravel()[idx]) < 1e-6 * (1 + abs(fd))
+
+
 def test_sensitivity_is_backprojection_of_ones():
     g = geom3d(6, 3, 9, 6, ntof=4, tof_sigma=6.0, tof_bin=8.0)
     G, x, m, _, _ = _problem(g)
