@@ -1,16 +1,19 @@
-"""Benchmark of the subset-gradient path on the 3D non-TOF brain workload.
+"""Benchmark of the subset-gradient path of RDP-regularised PET reconstruction.
 
-Workload (config "c2"): 128x128x47 image (2x2x2.8 mm), cylindrical scanner sinogram 250
-radial x 168 views x 109 planes, seeded brain-like phantom, 1e7 counts, 20% smooth
-background, 21 view subsets.  One STEP is one SVRG outer loop of Algorithm 1: the
-harmonic preconditioner update (eq. 8), a snapshot refresh (21 subset gradients) and
-41 inner iterations (eq. 9 + eq. 6), i.e. 62 subset gradients (forward projection,
-KL ratio, backprojection and RDP gradient) per step.
+Headline workload (c5, brain-scale TOF): 215x215x71 image (1.3x1.3x2.0 mm), cylindrical
+scanner sinogram 357 radial x 224 views x 1293 planes x 13 TOF bins (1.34 G bins, uint16
+counts, 3e8 total, 20% smooth background), 25 view subsets (24 of 9 views, 1 of 8),
+generated on the device.  One STEP is one SVRG outer loop of Algorithm 1: the harmonic
+preconditioner update (eq. 8), a snapshot refresh (25 subset gradients) and 49 inner
+iterations (eq. 9 + eq. 6), i.e. 74 subset gradients (TOF forward projection, KL
+ratio, backprojection and RDP gradient) per step.  The JSON line also carries the same
+measurement on the 3D non-TOF workload (c2: 128x128x47, 250 x 168 x 109, 21 subsets,
+62 subset gradients per step) and the time to 1% NRMSE against converged oracle images.
 
 Metric: subset gradients per second (whole job: all ranks).  Multi-GPU runs are
 independent replicas (one reconstruction per rank, no collective on the data path).
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload c5|c2]
 """
 from __future__ import annotations
 
@@ -30,14 +33,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "subset grads/s (fwd+back+RDP) & % HBM roofline; time to 1% NRMSE vs oracle"
 UNIT = "subset_grads/s"
-WORKLOAD = ("c2: 3D non-TOF 128x128x47 (2x2x2.8 mm), sinogram 250 radial x 168 views x 109 planes "
-            "(span-3 segments 0 and +-9), 1e7 counts, 21 subsets, SVRG + harmonic preconditioner")
+WORKLOADS = {
+    "c5": ("c5: 3D TOF brain-scale 215x215x71 (1.3x1.3x2 mm), sinogram 357 radial x 224 views x 1293 "
+           "planes (36 rings, span 1) x 13 TOF bins (1.34 G bins), uint16 counts (3e8), 25 subsets "
+           "(24 of 9 views, 1 of 8), SVRG + harmonic preconditioner"),
+    "c2": ("c2: 3D non-TOF 128x128x47 (2x2x2.8 mm), sinogram 250 radial x 168 views x 109 planes "
+           "(span-3 segments 0 and +-9), 1e7 counts, 21 subsets, SVRG + harmonic preconditioner"),
+}
+WORKLOAD = WORKLOADS["c5"]
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
@@ -50,8 +59,12 @@ def parse():
                          "study: epochs to 1%% NRMSE over algorithm x preconditioner x tau0 (2D)")
     ap.add_argument("--shape", default="auto",
                     help="grad mode: 'auto' (autotuner) or 'K,S' planes per thread, parts per LOR")
-    ap.add_argument("--config", default="c2", choices=["c2", "c3"],
-                    help="grad mode: c2 (non-TOF, 1e7 counts) or c3 (11 TOF bins, 1e6 counts)")
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c5"],
+                    help="grad mode: c2 (non-TOF, 1e7 counts), c3 (11 TOF bins, 1e6 counts) or c5 "
+                         "(13 TOF bins, 1.34 G bins, generated on the device)")
+    ap.add_argument("--workload", default="c5", choices=["c5", "c2"],
+                    help="step mode: the workload of the headline line (the other one is added as a key)")
+    ap.add_argument("--no-c2", action="store_true", help="step mode: skip the secondary c2 measurement")
     ap.add_argument("--study-config", default="c1", choices=["c1", "c2", "c2s", "c2s16", "c3s"],
                     help="study mode: workload with a converged reference image in tests/golden")
     return ap.parse_args()
@@ -174,19 +187,31 @@ class Clocks:
                 "samples": len(load)}
 
 
-def make_inputs(seed):
+def load_workload(cfg, seed, dev):
+    """(problem dict, device tensors y, r, mu, sens) of a workload: c5 is generated on the
+    device (its 1.34 G TOF bins do not fit the host generator), the others on the host."""
+    import torch
     from paper_2506_04976_gb300 import synth
-    return synth.make_problem("c2", seed)
+    if cfg == "c5":
+        p = synth.make_problem_device("c5", seed, device=dev)
+        dt = dict(y=p["y"], r=p["r"], sens=p["sens"], mu=torch.from_numpy(p["mu"].astype(np.float32)).to(dev))
+    else:
+        p = synth.make_problem(cfg, seed)
+        y = p["y"].view(np.int16) if p["y"].dtype == np.uint16 else p["y"].astype(np.int32)
+        dt = dict(y=torch.from_numpy(y).to(dev), r=torch.from_numpy(p["r"]).to(dev),
+                  mu=torch.from_numpy(p["mu"].astype(np.float32)).to(dev),
+                  sens=torch.from_numpy(p["sens"].astype(np.float32)).to(dev))
+    return p, dt
 
 
-def algorithmic_bytes_per_grad(p):
-    """Fused subset gradient: counts (u16) + background (f32) + factors m (f32) per LOR of
-    one subset, one read of the image and one write of the gradient (f32)."""
+def algorithmic_bytes_per_grad(p, y_itemsize=2):
+    """Fused subset gradient, averaged over the n subsets: counts and background (f32) per
+    TOF bin, factors m (f32) per LOR, one read of the image and one write of the gradient."""
     g = p["geom"]
-    n = p["nsub"]
-    lors = (g["nview"] // n) * len(g["z1"]) * g["nrad"]
+    T = g["ntof"] if g["ntof"] > 1 else 1
+    lors = g["nview"] * len(g["z1"]) * g["nrad"] / p["nsub"]
     N = g["nx"] * g["ny"] * g["nz"]
-    return lors * (p["y"].itemsize + 4 + 4) + 2 * 4 * N
+    return lors * (T * (y_itemsize + 4) + 4) + 2 * 4 * N
 
 
 def cpu_baseline(p, seconds, steps=None):
@@ -214,22 +239,82 @@ def cpu_baseline(p, seconds, steps=None):
     return times
 
 
+def oracle_workers():
+    return max(1, min(16, os.cpu_count() or 1))
+
+
+def oracle_sampled_rate(p, subset=0, planes_every=1, workers=None):
+    """The FP64 oracle on a bounded sample of a device-generated workload: the data term
+    and gradient of the first view of `subset` over every `planes_every`-th plane, split
+    over host processes (oracle.pieces; the slowest worker's compute time), scaled to a
+    whole subset by its LOR count, plus one single-threaded RDP gradient of the image."""
+    import torch
+    import oracle as O
+    from oracle import pieces
+    g = p["geom"]
+    n = p["nsub"]
+    workers = workers or oracle_workers()
+    views = O.subset_views(g["nview"], n, subset)
+    v = int(views[0])
+    P = len(g["z1"])
+    sel = np.arange(0, P, planes_every)
+    gk = dict(g, z1=np.asarray(g["z1"])[sel], z2=np.asarray(g["z2"])[sel])
+    si = torch.from_numpy(sel.astype(np.int64)).to(p["y"].device)
+    y = p["y"][v].index_select(0, si).cpu().numpy()
+    y = y.view(np.uint16) if y.dtype == np.int16 else y
+    r = p["r"][v].index_select(0, si).cpu().numpy()
+    sens = p["sens"][v].index_select(0, si).cpu().numpy()
+    x = np.maximum(p["x_true"], 0.05 * p["x_true"].max()).astype(np.float32)
+    timing = {}
+    pieces.data_grad_subset(gk, [v], x, p["mu"].astype(np.float32), sens[None], r[None], y[None],
+                            workers=workers, chunk=-(-len(sel) // workers), timing=timing)
+    t0 = time.perf_counter()
+    O.rdp(x.astype(np.float64), (g["dx"], g["dy"], g["dz"]), p["gamma"], p["eps"])
+    t_rdp = time.perf_counter() - t0
+    frac = len(sel) / (len(views) * P)
+    t_grad = timing["seconds"] / frac + t_rdp
+    sample = (f"FP64 oracle: data term + gradient of view {v} of subset {subset} over {len(sel)} of {P} planes "
+              f"(all {g['nrad']} radial bins x {g['ntof']} TOF bins; {frac:.4f} of the subset's LORs) in "
+              f"{timing['workers']} processes ({timing['seconds']:.2f} s, slowest worker), scaled by the LOR "
+              f"count, + one single-threaded RDP gradient ({t_rdp:.2f} s)")
+    return {"value": 1.0 / t_grad, "unit": UNIT, "cores": timing["workers"], "kind": "oracle", "sample": sample}
+
+
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle as it stands on the host cores, on a bounded
+    sample of the headline workload per step (rank 0 only)."""
     if rank != 0:
         return
-    p = make_inputs(0)
-    # warm-up and timed steps: each step is one whole subset gradient in the oracle
-    cpu_baseline(p, 0, steps=args.warmup) if args.warmup > 0 else None
-    times = cpu_baseline(p, 0, steps=args.steps)
+    cfg = getattr(args, "workload", "c5")
+    if cfg == "c5":
+        import torch
+        dev = torch.device("cuda", 0)
+        from paper_2506_04976_gb300 import synth
+        p = synth.make_problem_device("c5", 0, device=dev)
+        torch.cuda.synchronize()
+        rates = []
+        for k in range(args.warmup + args.steps):
+            r = oracle_sampled_rate(p, subset=k % p["nsub"], planes_every=2)
+            if k >= args.warmup:
+                rates.append(r)
+        times = [1.0 / r["value"] for r in rates]
+        cores = rates[-1]["cores"]
+        sample = f"per step: {rates[-1]['sample']}"
+    else:
+        from paper_2506_04976_gb300 import synth
+        p = synth.make_problem(cfg, 0)
+        cpu_baseline(p, 0, steps=args.warmup) if args.warmup > 0 else None
+        times = cpu_baseline(p, 0, steps=args.steps)
+        cores = 1
+        sample = f"{len(times)} full-size subset gradients (fwd+back+RDP), FP64, 1 thread"
     total = sum(times)
     value = len(times) / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "step": "one subset gradient"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{len(times)} full-size subset gradients (fwd+back+RDP), FP64, 1 thread"},
+        "data": "synthetic", "config": {"workload": WORKLOADS[cfg], "step": "one subset gradient"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -590,6 +675,139 @@ def run_grad_only(args, pet, dev):
                       "ms_per_call": a.elapsed_time(b) / max(args.steps, 1)}))
 
 
+def kernel_name(T, shape):
+    if T > 1:
+        return f"k_grad_tofw<{T},{shape[1]}>" if T in (11, 13) else f"k_grad<{T},{shape[1]}>"
+    return f"k_grad_mp<{shape[0]},{shape[1]}>" if shape[0] > 1 else f"k_grad<1,{shape[1]}>"
+
+
+def issue_peak():
+    """Instruction-issue roofline: 152 SMs x 4 schedulers x 1 warp instruction per cycle at
+    the maximum SM clock."""
+    sm_max = 2070.0
+    mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(mp):
+        sm_max = float(json.load(open(mp)).get("sm_max_mhz", sm_max))
+    return 152 * 4 * sm_max * 1e6
+
+
+def measure_svrg(pet, dev, cfg, p, dt, args, rank, world, pg, e2e=True, clk=None):
+    """SVRG outer loops (harmonic preconditioner update, refresh of n subset gradients,
+    2n - 1 inner iterations) of one workload: device-timed rate with the L2 flushed
+    between steps, the fused kernel's live launch time, and the end-to-end rate through
+    the C ABI with the step's inputs copied from pinned host memory every step."""
+    import torch
+    g = p["geom"]
+    n = p["nsub"]
+    T = g["ntof"] if g["ntof"] > 1 else 1
+    step_len = 2 * n                      # one SVRG outer loop (omega = 2)
+    grads_per_step = 3 * n - 1            # n at the refresh + (2n - 1) inner iterations
+    plan = pet.Plan(g, n)
+    plan.set_data(dt["y"], dt["r"], dt["mu"], dt["sens"])
+    shape = plan.autotune()
+    x0 = torch.ones(plan.img_shape, device=dev)
+    for s in range(n):  # one OSEM epoch from a uniform image (Sec. 3.1 initialisation)
+        plan.em_update(x0, s)
+    total_steps = args.warmup + args.steps + (args.steps if e2e else 0)
+    pcs = [k * step_len for k in range(total_steps + 1)]
+    solver = pet.Solver(plan, algo=pet.SVRG, omega=2, step_rule=pet.STEP_VANISH, tau0=1.0, eta=0.02,
+                        precond_kind=1, alpha=1.0, delta_rel=1e-6, pc_iters=pcs, beta=p["beta"],
+                        gamma=p["gamma"], eps=p["eps"], seed=1234 + rank, use_graph=True)
+    solver.set_image(x0)
+    solver.profile(True)
+    flush = torch.empty(64 * 1024 * 1024, device=dev)  # 256 MB > L2 (129 MB)
+    for _ in range(args.warmup):
+        solver.run(step_len)
+    torch.cuda.synchronize()
+    solver.kernel_time()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kern_ms, kern_n = 0.0, 0
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    launches0 = pet.launch_count()
+    wall0 = time.perf_counter()
+    if clk:
+        clk.__enter__()
+    try:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record()
+            solver.run(step_len)
+            ev[i][1].record()
+            torch.cuda.synchronize()
+            ms, nl = solver.kernel_time()
+            kern_ms += ms
+            kern_n += nl
+        torch.cuda.synchronize()
+    finally:
+        if clk:
+            clk.__exit__(None, None, None)
+    wall = time.perf_counter() - wall0
+    launches = pet.launch_count() - launches0
+    if pg:
+        pg.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = max_over_ranks(pg, sum(step_ms) / 1e3, dev)
+    out = {"value": whole_job_rate(grads_per_step * args.steps, world, t_total),
+           "ms_per_step": 1e3 * t_total / args.steps, "wall_s_timed": wall, "gpu_launches": launches,
+           "grads_per_step": grads_per_step, "shape": shape, "kernel_ms": kern_ms / max(kern_n, 1),
+           "kernel_launches": kern_n, "T": T, "y_itemsize": dt["y"].element_size()}
+    if e2e:
+        y_host = torch.empty(dt["y"].shape, dtype=dt["y"].dtype, pin_memory=True)
+        r_host = torch.empty(dt["r"].shape, dtype=dt["r"].dtype, pin_memory=True)
+        y_host.copy_(dt["y"])
+        r_host.copy_(dt["r"])
+        x0_host = x0.cpu().pin_memory()
+        x_dev = torch.empty_like(x0)
+        xo = torch.empty(plan.img_shape, pin_memory=True)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            dt["y"].copy_(y_host, non_blocking=True)
+            dt["r"].copy_(r_host, non_blocking=True)
+            x_dev.copy_(x0_host, non_blocking=True)
+            solver.set_image(x_dev)
+            solver.run(step_len)
+            xo.copy_(solver.image(), non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        te = max_over_ranks(pg, a.elapsed_time(b) / 1e3, dev)
+        out["e2e"] = {"value": whole_job_rate(grads_per_step * args.steps, world, te), "unit": UNIT,
+                      "h2d_bytes_per_step": int(y_host.numel() * y_host.element_size() + r_host.numel() * 4 +
+                                                x0_host.numel() * 4),
+                      "d2h_bytes_per_step": int(xo.numel() * 4)}
+        solver.kernel_time()
+        del y_host, r_host
+    del solver, plan
+    return out
+
+
+def roofline_of(cfg, p, m):
+    """Roofline figures of the fused subset-gradient kernel from its live launch time."""
+    peak, peak_kind = measured_peaks()
+    kavg = m["kernel_ms"]
+    abytes = algorithmic_bytes_per_grad(p, m["y_itemsize"])
+    achieved = abytes / (kavg * 1e-3) / 1e9
+    kname = kernel_name(m["T"], m["shape"])
+    tag = f"k_grad_{cfg}"
+    what = "TOF forward, KL ratio, TOF backprojection" if m["T"] > 1 else "forward, KL ratio, backprojection"
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": ncu_traffic(tag, kname), "kernel": f"{kname} (fused {what} of one subset)",
+            "kernel_ms": kavg, "launches_timed": m["kernel_launches"], "algorithmic_bytes": abytes,
+            "peak_kind": f"hbm_gbs {peak_kind}",
+            "launch_shape": {"planes_per_thread": m["shape"][0], "parts_per_lor": m["shape"][1]}}
+    inst = ncu_instructions(tag, kname)
+    if inst is not None:
+        ipeak = issue_peak()
+        ach = inst / (kavg * 1e-3)
+        roof["issue"] = {"achieved": ach, "peak": ipeak, "unit": "warp instructions/s", "frac": ach / ipeak,
+                         "instructions_per_launch": inst, "source": "ncu smsp__inst_executed.sum"}
+    return roof
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -617,139 +835,53 @@ def main():
         return run_batched(args, pet, dev)
     if args.mode == "c5":
         return run_c5(args, pet, dev)
-    p = make_inputs(rank)
-    g = p["geom"]
-    n = p["nsub"]
-    step_len = 2 * n                      # one SVRG outer loop (omega = 2)
-    grads_per_step = 3 * n - 1            # n at the refresh + (2n - 1) inner iterations
-    plan = pet.Plan(g, n)
-    y_host = torch.from_numpy(p["y"].view(np.int16)).pin_memory()
-    r_host = torch.from_numpy(p["r"]).pin_memory()
-    y = y_host.to(dev)
-    r = r_host.to(dev)
-    plan.set_data(y, r, torch.from_numpy(p["mu"].astype(np.float32)).to(dev),
-                  torch.from_numpy(p["sens"].astype(np.float32)).to(dev))
-    shape = plan.autotune()
-    # one OSEM epoch from a uniform image (Sec. 3.1 initialisation)
-    x0 = torch.ones(plan.img_shape, device=dev)
-    for s in range(n):
-        plan.em_update(x0, s)
-    x0_host = x0.cpu().pin_memory()
-    total_steps = args.warmup + args.steps + (0 if args.no_e2e else args.steps)
-    pcs = [k * step_len for k in range(total_steps + 1)]
-    solver = pet.Solver(plan, algo=pet.SVRG, omega=2, step_rule=pet.STEP_VANISH, tau0=1.0, eta=0.02,
-                        precond_kind=1, alpha=1.0, delta_rel=1e-6, pc_iters=pcs, beta=p["beta"],
-                        gamma=p["gamma"], eps=p["eps"], seed=1234 + rank, use_graph=True)
-    solver.set_image(x0)
-    solver.profile(True)
-    flush = torch.empty(64 * 1024 * 1024, device=dev)  # 256 MB > L2 (129 MB)
-
-    for _ in range(args.warmup):
-        solver.run(step_len)
-    torch.cuda.synchronize()
-    solver.kernel_time()
-
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    kern_ms, kern_n = 0.0, 0
     import tempfile
+    cfg = args.workload
+    p, dt = load_workload(cfg, rank, dev)
+    torch.cuda.synchronize()
     clk = Clocks(os.path.join(tempfile.gettempdir(), f"pet_bench_clocks_rank{rank}.csv"))
-    if pg:
-        pg.barrier()
-    torch.cuda.synchronize()
-    launches0 = pet.launch_count()
-    wall0 = time.perf_counter()
-    with clk:
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record()
-            solver.run(step_len)
-            ev[i][1].record()
-            torch.cuda.synchronize()
-            ms, nl = solver.kernel_time()
-            kern_ms += ms
-            kern_n += nl
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    launches = pet.launch_count() - launches0
-    if pg:
-        pg.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_total = max_over_ranks(pg, sum(step_ms) / 1e3, dev)
-    value = whole_job_rate(grads_per_step * args.steps, world, t_total)
-
-    # end to end through the C ABI from pinned host buffers
-    e2e = None
-    if not args.no_e2e:
-        x_dev = torch.empty_like(x0)
-        xo = torch.empty(plan.img_shape, pin_memory=True)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(args.steps):
-            y.copy_(y_host, non_blocking=True)
-            r.copy_(r_host, non_blocking=True)
-            x_dev.copy_(x0_host, non_blocking=True)
-            solver.set_image(x_dev)
-            solver.run(step_len)
-            xo.copy_(solver.image(), non_blocking=True)
-        b.record()
-        torch.cuda.synchronize()
-        te = max_over_ranks(pg, a.elapsed_time(b) / 1e3, dev)
-        e2e = {"value": whole_job_rate(grads_per_step * args.steps, world, te), "unit": UNIT,
-               "h2d_bytes_per_step": int(y_host.numel() * 2 + r_host.numel() * 4 + x0_host.numel() * 4),
-               "d2h_bytes_per_step": int(xo.numel() * 4)}
-        solver.kernel_time()
-
+    m = measure_svrg(pet, dev, cfg, p, dt, args, rank, world, pg, e2e=not args.no_e2e, clk=clk)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        if cfg == "c5":
+            cpu = oracle_sampled_rate(p)
+        else:
+            times = cpu_baseline(p, args.cpu_seconds)
+            cpu = {"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{len(times)} full-size {cfg} subset gradients (fwd+back+RDP), FP64, 1 thread"}
+    del dt
+    other = None
+    if not args.no_c2:
+        ocfg = "c2" if cfg == "c5" else "c5"
+        po, dto = load_workload(ocfg, rank, dev)
+        mo = measure_svrg(pet, dev, ocfg, po, dto, args, rank, world, pg, e2e=False)
+        other = {"workload": WORKLOADS[ocfg], "value": mo["value"], "unit": UNIT, "ms_per_step": mo["ms_per_step"],
+                 "step": f"SVRG outer loop = {mo['grads_per_step']} subset gradients",
+                 "roofline": roofline_of(ocfg, po, mo) if rank == 0 else None}
+        del dto
     if rank != 0:
         if pg:
             pg.destroy_process_group()
         return
-
-    peak, peak_kind = measured_peaks()
-    kavg = kern_ms / max(kern_n, 1)
-    abytes = algorithmic_bytes_per_grad(p)
-    achieved = abytes / (kavg * 1e-3) / 1e9
-    kname = f"k_grad_mp<{shape[0]},{shape[1]}>" if shape[0] > 1 else f"k_grad<1,{shape[1]}>"
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": ncu_traffic("k_grad_c2", kname),
-                "kernel": kname + " (fused forward, KL ratio, backprojection of one subset)",
-                "kernel_ms": kavg, "launches_timed": kern_n, "algorithmic_bytes": abytes,
-                "peak_kind": f"hbm_gbs {peak_kind}", "launch_shape": {"planes_per_thread": shape[0],
-                                                                      "parts_per_lor": shape[1]}}
-    # The kernel's working set is L2-resident; what bounds it is instruction issue.  Issue
-    # roofline: 152 SMs x 4 schedulers x 1 warp instruction per cycle at the maximum SM clock.
-    inst = ncu_instructions("k_grad_c2", kname)
-    if inst is not None:
-        sm_max = 2070.0
-        mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
-        if os.path.exists(mp):
-            sm_max = float(json.load(open(mp)).get("sm_max_mhz", sm_max))
-        ipeak = 152 * 4 * sm_max * 1e6
-        ach = inst / (kavg * 1e-3)
-        roofline["issue"] = {"achieved": ach, "peak": ipeak, "unit": "warp instructions/s", "frac": ach / ipeak,
-                             "instructions_per_launch": inst, "source": "ncu smsp__inst_executed.sum"}
-    cpu = None
-    if world == 1 and not args.no_cpu:
-        times = cpu_baseline(p, args.cpu_seconds)
-        cpu = {"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{len(times)} full-size c2 subset gradients (fwd+back+RDP), FP64, 1 thread"}
-    clocks = clk.summary()
     nrmse_times = {}
     if not args.no_nrmse:
-        for cfg in ("c1", "c2", "c2s", "c3s"):
-            t = time_to_nrmse(pet, dev, cfg)
+        for c in ("c1", "c2", "c2s", "c3s"):
+            t = time_to_nrmse(pet, dev, c)
             if t is not None:
-                nrmse_times[cfg] = t
+                nrmse_times[c] = t
+    n = p["nsub"]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "step": "SVRG outer loop: precond update + refresh + 41 inner "
-                   "iterations = 62 subset gradients", "l2": "flushed between steps (256 MB write)",
-                   "graph": "one CUDA graph per epoch", "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clocks, "wall_s_timed": wall, "time_to_1pct_nrmse": nrmse_times or None,
+        "config": {"workload": WORKLOADS[cfg],
+                   "step": f"SVRG outer loop: precond update + refresh ({n}) + {2 * n - 1} inner iterations = "
+                           f"{m['grads_per_step']} subset gradients",
+                   "l2": "flushed between steps (256 MB write)", "graph": "one CUDA graph per epoch",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": roofline_of(cfg, p, m), "cpu_baseline": cpu, "e2e": m.get("e2e"),
+        "gpu_launches": m["gpu_launches"], "clocks": clk.summary(), "wall_s_timed": m["wall_s_timed"],
+        ("c2" if cfg == "c5" else "c5"): other, "time_to_1pct_nrmse": nrmse_times or None,
     }
     print(json.dumps(line), flush=True)
     if pg:

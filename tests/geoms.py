@@ -31,3 +31,12 @@ def rand_img(g, seed, lo=0.0, hi=1.0):
 
 def rand_sino(g, seed, lo=0.5, hi=1.5):
     return synth.random_sinogram_like(g, seed, lo, hi)
+
+
+def make_spec_problem(args):
+    """(seed, spec) -> synth.make_problem(spec name, seed, **rest of spec); a module-level
+    function so that spawned worker processes can build batch instances in parallel."""
+    seed, spec = args
+    sp = dict(spec)
+    name = sp.pop("name")
+    return synth.make_problem(name, seed, **sp)

@@ -1,18 +1,26 @@
 """The large TOF workload at full size (215x215x71 image; 357 radial x 224 views x 1293
-planes x 13 TOF bins = 1.34 G bins; uint16 counts; 25 uneven subsets): sampled TOF LORs
-against the oracle, adjointness of one subset, and one whole subset gradient."""
+planes x 13 TOF bins = 1.34 G bins; uint16 counts; 25 uneven subsets): sampled TOF LORs,
+one whole view's forward projection and backprojection, and one whole subset's gradient
+and objective (eq. 5) against the FP64 oracle, which receives the device-generated data
+copied to the host and runs split over host processes (oracle.pieces); adjointness of
+one subset.  Tolerances as for the smaller workloads: projections within 1e-4 |ref| +
+1e-5 max|ref| per bin and 1e-5 in relative L2; gradients within 1e-5 of ||A_s^T 1|| in
+L2 and 1e-4 (A_s^T 1)_j + 1e-6 max(A_s^T 1) per voxel j; objective within 1e-5."""
+import os
 import time
 
 import numpy as np
 import pytest
 
 import oracle as O
+from oracle import pieces
 from paper_2506_04976_gb300 import synth
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 _S = {}
+WORKERS = min(16, os.cpu_count() or 1)
 
 
 def c5():
@@ -78,13 +86,65 @@ def test_c5_adjointness_one_subset():
         assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
 
 
-def test_c5_subset_gradient_finite_and_feasible():
+def _x(p):
+    return np.maximum(p["x_true"], 0.05 * p["x_true"].max()).astype(np.float32)
+
+
+def test_c5_whole_view_forward_and_backprojection_against_oracle():
+    """Every LOR and TOF bin of one view of subset 7 (461,601 LORs x 13 bins), forward and
+    back (A = m P with its TOF weights, Sec. 1.1), both backprojectors."""
     S = c5()
     p, plan = S["p"], S["plan"]
-    x = torch.from_numpy(np.maximum(p["x_true"], 0.05 * p["x_true"].max()).astype(np.float32)).to(DEV)
-    obj, g = plan.objective_grad(x, 3, prior=(p["beta"] / p["nsub"], p["gamma"], p["eps"]))
-    torch.cuda.synchronize()
+    g = p["geom"]
+    s, j = 7, 4
+    v = int(O.subset_views(g["nview"], p["nsub"], s)[j])
+    x = _x(p)
+    got = plan.forward(torch.from_numpy(x).to(DEV), s)[j].cpu().numpy()
+    sens_v = p["sens"][v].cpu().numpy()
+    mu32 = p["mu"].astype(np.float32)
+    ref = pieces.forward_view(g, v, x, mu32, sens_v, workers=WORKERS)
+    assert got.shape == ref.shape == (1293, 357, 13)
+    assert np.all(np.abs(got - ref) <= 1e-4 * np.abs(ref) + 1e-5 * np.abs(ref).max())
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+    gen = torch.Generator(device=DEV).manual_seed(21)
+    q = torch.zeros(plan.subset_shape(s), device=DEV)
+    q[j] = 0.5 + torch.rand(q.shape[1:], device=DEV, generator=gen)
+    ref_b = pieces.back_view(g, v, q[j].cpu().numpy(), mu32, sens_v, workers=WORKERS)
+    for det in (False, True):
+        gb = plan.back(q, s, deterministic=det).cpu().numpy()
+        assert np.all(np.abs(gb - ref_b) <= 1e-4 * np.abs(ref_b) + 1e-5 * np.abs(ref_b).max()), det
+        assert np.linalg.norm(gb - ref_b) <= 1e-5 * np.linalg.norm(ref_b), det
+
+
+def test_c5_whole_subset_gradient_and_objective_against_oracle():
+    """The fused subset gradient and objective of the 8-view subset (3.69 M LORs x 13 TOF
+    bins) with the prior's share (beta/n) S, against the oracle's data term (eq. 5) plus
+    its RDP (eq. 3)."""
+    S = c5()
+    p, plan = S["p"], S["plan"]
+    g = p["geom"]
+    s = 24
+    n = p["nsub"]
+    views = O.subset_views(g["nview"], n, s)
+    assert len(views) == 8
+    x = _x(p)
+    xt = torch.from_numpy(x).to(DEV)
+    obj, gg = plan.objective_grad(xt, s, prior=(p["beta"] / n, p["gamma"], p["eps"]))
+    gg = gg.cpu().numpy()
+    obj = float(obj)
     plan.check()
-    assert torch.isfinite(g).all() and np.isfinite(float(obj))
-    # the gradient of a subset term is bounded by its sensitivity (q <= m per bin)
-    assert float(g.max()) <= float(plan.sensitivity(3).max()) * 1.0001 + p["beta"]
+    vi = torch.from_numpy(views.astype(np.int64)).to(DEV)
+    y_c = p["y"].index_select(0, vi).cpu().numpy().view(np.uint16)
+    r_c = p["r"].index_select(0, vi).cpu().numpy()
+    sens_c = p["sens"].index_select(0, vi).cpu().numpy()
+    mu32 = p["mu"].astype(np.float32)
+    val, gd = pieces.data_grad_subset(g, views, x, mu32, sens_c, r_c, y_c, workers=WORKERS)
+    ones = np.ones(y_c.shape, np.float32)
+    scale = pieces.back_views(g, views, ones, mu32, sens_c, workers=WORKERS)  # A_s^T 1
+    Sv, gs, _ = O.rdp(x.astype(np.float64), (g["dx"], g["dy"], g["dz"]), p["gamma"], p["eps"])
+    ref = gd + p["beta"] / n * gs
+    ref_val = val + p["beta"] / n * Sv
+    d = np.abs(gg - ref)
+    assert np.linalg.norm(d) <= 1e-5 * np.linalg.norm(scale)
+    assert np.all(d <= 1e-4 * scale + 1e-6 * scale.max())
+    assert abs(obj - ref_val) <= 1e-5 * abs(ref_val)

@@ -105,6 +105,34 @@ def test_compact_view_pieces_add_up_to_the_subset_data_term(tof):
         assert abs(fd - gk.ravel()[idx]) < 1e-6 * (1 + abs(fd))
 
 
+def test_process_pieces_reproduce_the_oracle():
+    """oracle.pieces (the oracle split over spawned processes, one view and a run of planes
+    per piece) gives the single-process oracle's subset data term, gradient, forward
+    projection and backprojection of one view."""
+    from oracle import pieces
+    g = geom3d(6, 3, 9, 6, ntof=4, tof_sigma=6.0, tof_bin=8.0)
+    G = O.Geometry(g)
+    x = rand_img(g, 8, 0.5, 2.0)
+    mu = rand_img(g, 9, 0.0, 0.01)
+    sens = rand_sino(g, 10, 0.8, 1.2)[..., 0]
+    r = rand_sino(g, 11, 0.1, 0.3)
+    y = np.floor(rand_sino(g, 12, 0.0, 3.0))
+    m = O.multiplicative(G, mu, sens)
+    nsub, s = 3, 2
+    views = O.subset_views(g["nview"], nsub, s)
+    val, grad = O.data_grad(G, nsub, s, x, m, r, y)
+    pv, pg = pieces.data_grad_subset(g, views, x, mu, sens[views], r[views], y[views], workers=2, chunk=2)
+    assert abs(pv - val) <= 1e-12 * abs(val)
+    assert np.allclose(pg, grad, rtol=1e-12, atol=1e-12 * np.abs(grad).max())
+    v = int(views[1])
+    fwd = pieces.forward_view(g, v, x, mu, sens[v], workers=2, chunk=2)
+    assert np.allclose(fwd, m[v][..., None] * O.project(G, x, [v])[0], rtol=1e-12, atol=0)
+    q = rand_sino(g, 13, -1.0, 1.0)[v]
+    bk = pieces.back_view(g, v, q, mu, sens[v], workers=2, chunk=2)
+    assert np.allclose(bk, O.backproject(G, (m[v][..., None] * q)[None], [v]), rtol=1e-12,
+                       atol=1e-13 * np.abs(bk).max())
+
+
 def test_sensitivity_is_backprojection_of_ones():
     g = geom3d(6, 3, 9, 6, ntof=4, tof_sigma=6.0, tof_bin=8.0)
     G, x, m, _, _ = _problem(g)
