@@ -361,8 +361,9 @@ double o_data_grad(const og_geom *g, int nsub, int s, const double *x, const dou
           double ybar = m[lor] * px[loc * T + b] + rr[lor * T + b];
           double yy = y[lor * T + b];
           val += o_kl_term(ybar, yy);
-          /* d/ds d(s,t) = 1 - t/s; chain rule through A = m P */
-          q[loc * T + b] = m[lor] * (1.0 - yy / ybar);
+          /* d/ds d(s,t) = 1 - t/s for t > 0 and d/ds d(s,0) = 1 (d(s,0) = s, also at
+             s = 0); chain rule through A = m P */
+          q[loc * T + b] = m[lor] * (yy > 0 ? 1.0 - yy / ybar : 1.0);
         }
       }
   if (grad) o_backproject(g, views, nv, q, grad);
@@ -390,7 +391,7 @@ double o_data_grad_views(const og_geom *g, const int *views, int nv, const doubl
       double ybar = m_c[l] * px[l * T + b] + r_c[l * T + b];
       double yy = y_c[l * T + b];
       val += o_kl_term(ybar, yy);
-      q[l * T + b] = m_c[l] * (1.0 - yy / ybar);
+      q[l * T + b] = m_c[l] * (yy > 0 ? 1.0 - yy / ybar : 1.0);
     }
   if (grad && o_backproject(g, views, nv, q, grad) != 0) rc = -1;
   free(px); free(q);
@@ -842,7 +843,8 @@ void o_em_update(const og_geom *g, int nsub, int s, const double *m, const doubl
         size_t loc = ((size_t)j * g->nplane + p) * g->nrad + r;
         for (int b = 0; b < T; b++) {
           double ybar = m[lor] * px[loc * T + b] + rr[lor * T + b];
-          q[loc * T + b] = m[lor] * y[lor * T + b] / ybar;
+          /* bins with y = 0 add nothing to A^T (y / ybar), also where ybar = 0 */
+          q[loc * T + b] = y[lor * T + b] > 0 ? m[lor] * y[lor * T + b] / ybar : 0.0;
         }
       }
   o_backproject(g, views, nv, q, bp);

@@ -133,6 +133,26 @@ def test_process_pieces_reproduce_the_oracle():
                        atol=1e-13 * np.abs(bk).max())
 
 
+@pytest.mark.parametrize("tof", [1, 4])
+def test_empty_bins_without_background(tof):
+    """Bins with y = 0 and ybar = 0 (LORs that miss the object, no background): the KL
+    term d(s, 0) = s of Sec. 1.2 is 0 there and its derivative is 1, so with a zero image,
+    zero background and no counts the data term vanishes and its gradient is A^T 1; the
+    EM update leaves the zero image at zero."""
+    g = geom3d(6, 3, 9, 6, ntof=tof, tof_sigma=6.0, tof_bin=8.0)
+    G = O.Geometry(g)
+    m = 0.5 + 0.5 * rand_sino(g, 14, 0, 1)[..., 0]
+    z = np.zeros(G.sino_shape)
+    x = np.zeros(G.img_shape)
+    val, grad = O.data_grad(G, 3, 1, x, m, z, z)
+    assert val == 0.0 and np.isfinite(grad).all()
+    assert np.allclose(grad, O.sensitivity(G, 3, 1, m), rtol=1e-14, atol=0)
+    views = O.subset_views(g["nview"], 3, 1)
+    vv, gv = O.data_grad_views(G, views, x, m[views], z[views], z[views])
+    assert vv == 0.0 and np.allclose(gv, grad, rtol=1e-14, atol=0)
+    assert np.array_equal(O.em_update(G, 3, 1, m, z, z, x), x)
+
+
 def test_sensitivity_is_backprojection_of_ones():
     g = geom3d(6, 3, 9, 6, ntof=4, tof_sigma=6.0, tof_bin=8.0)
     G, x, m, _, _ = _problem(g)
