@@ -102,7 +102,7 @@ def measured_peaks():
 
 def source_hash():
     h = hashlib.sha256()
-    for f in ("proj_kernels.cu", "pet_internal.cuh"):
+    for f in ("proj_kernels.cu", "tof_kernels.cu", "pet_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2506_04976_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -192,8 +192,8 @@ def load_workload(cfg, seed, dev):
     device (its 1.34 G TOF bins do not fit the host generator), the others on the host."""
     import torch
     from paper_2506_04976_gb300 import synth
-    if cfg == "c5":
-        p = synth.make_problem_device("c5", seed, device=dev)
+    if cfg in ("c3", "c5"):
+        p = synth.make_problem_device(cfg, seed, device=dev)
         dt = dict(y=p["y"], r=p["r"], sens=p["sens"], mu=torch.from_numpy(p["mu"].astype(np.float32)).to(dev))
     else:
         p = synth.make_problem(cfg, seed)
@@ -649,12 +649,9 @@ def run_grad_only(args, pet, dev):
     """Subset gradients only (objective_grad on successive subsets), for ncu captures."""
     import torch
     from paper_2506_04976_gb300 import synth
-    p = synth.make_problem(args.config, 0)
+    p, dt = load_workload(args.config, 0, dev)
     plan = pet.Plan(p["geom"], p["nsub"])
-    y = p["y"].view(np.int16) if p["y"].dtype == np.uint16 else p["y"].astype(np.int32)
-    plan.set_data(torch.from_numpy(y).to(dev), torch.from_numpy(p["r"]).to(dev),
-                  torch.from_numpy(p["mu"].astype(np.float32)).to(dev),
-                  torch.from_numpy(p["sens"].astype(np.float32)).to(dev))
+    plan.set_data(dt["y"], dt["r"], dt["mu"], dt["sens"])
     if args.shape == "auto":
         shape = plan.autotune()
     else:
@@ -675,9 +672,24 @@ def run_grad_only(args, pet, dev):
                       "ms_per_call": a.elapsed_time(b) / max(args.steps, 1)}))
 
 
-def kernel_name(T, shape):
+def tof_window(geom):
+    """Bins a TOF sample can meet, as the library's windowed TOF kernel counts them (its
+    weight table has 1024 rows per bin width); 0 without TOF."""
+    T = geom.get("ntof", 1)
+    if T <= 1:
+        return 0
+    w, sig = geom["tof_bin"], geom["tof_sigma"]
+    ktab = math.ceil(2.0 * (3.0 * sig + 0.5 * w) / (w / 1024))
+    return (ktab - 1) // 1024 + 1
+
+
+def kernel_name(geom, shape):
+    T = geom.get("ntof", 1)
     if T > 1:
-        return f"k_grad_tofw<{T},{shape[1]}>" if T in (11, 13) else f"k_grad<{T},{shape[1]}>"
+        win = tof_window(geom)
+        if T <= 16 and win <= 8:
+            return f"k_grad_tofk<{shape[0]},{4 if win <= 4 else 6 if win <= 6 else 8},{shape[1]}>"
+        return f"k_grad<{16 if T <= 16 else 32},{shape[1]}>"
     return f"k_grad_mp<{shape[0]},{shape[1]}>" if shape[0] > 1 else f"k_grad<1,{shape[1]}>"
 
 
@@ -791,7 +803,7 @@ def roofline_of(cfg, p, m):
     kavg = m["kernel_ms"]
     abytes = algorithmic_bytes_per_grad(p, m["y_itemsize"])
     achieved = abytes / (kavg * 1e-3) / 1e9
-    kname = kernel_name(m["T"], m["shape"])
+    kname = kernel_name(p["geom"], m["shape"])
     tag = f"k_grad_{cfg}"
     what = "TOF forward, KL ratio, TOF backprojection" if m["T"] > 1 else "forward, KL ratio, backprojection"
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

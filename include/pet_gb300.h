@@ -110,12 +110,15 @@ const float *pet_plan_mult(const pet_plan *plan);
 /* Sensitivity image A_s^T 1 (s = -1: all views) owned by the plan. */
 const float *pet_plan_sensitivity(const pet_plan *plan, int subset);
 
-/* Launch shape of the fused subset-gradient kernel: planes per thread (1, 2 or 4; more
- * than 1 only without TOF: those LORs of one view and radial bin share their in-plane
- * sample positions) and parts per LOR (1, 2, 4, 8 or 16: interleaved sets of the
- * driving planes of one LOR processed by different threads; 16 only without TOF, 8 only
- * without TOF or with 11 or 13 TOF bins).  0 selects the built-in heuristic.  Results
- * are the same up to FP32 summation order.  PET_ERR_ARG for an unsupported shape. */
+/* Launch shape of the fused subset-gradient kernel: planes per thread (LORs of one view
+ * and radial bin on different planes share their in-plane sample positions: 1, 2 or 4
+ * without TOF; 1 or 2 with TOF when a sample meets at most 8 TOF bins, i.e. (6 sigma +
+ * w)/w <= 8 for bin width w, and ntof <= 16 (the windowed TOF kernel; the two planes of a
+ * thread then have equal axial slope and share their TOF weights); else 1) and parts per
+ * LOR (1, 2, 4, 8 or 16: interleaved sets of the driving planes of one LOR processed by
+ * different threads; 16 only without TOF; 8 without TOF, with the windowed TOF kernel or
+ * with 11 or 13 TOF bins; else up to 4).  0 selects the built-in heuristic.  Results are
+ * the same up to FP32 summation order.  PET_ERR_ARG for an unsupported shape. */
 pet_status pet_plan_set_grad_shape(pet_plan *plan, int planes_per_thread, int parts);
 
 /* Autotuner: times every valid launch shape on subset 0 of the bound data (a uniform

@@ -61,6 +61,8 @@ static void plan_free(pet_plan *p) {
   cudaFree(p->d_fpart); cudaFree(p->d_fscalar); cudaFree(p->d_qtmp); cudaFree(p->d_img);
   cudaFree(p->d_groups); cudaFree(p->d_gzd); cudaFree(p->d_gplane); cudaFree(p->d_gzs);
   cudaFree(p->d_erfc_tab);
+  cudaFree(p->d_tofw_tab);
+  cudaFree(p->d_tof_grp2);
   cudaFree(p->d_xs); cudaFree(p->d_rtmp);
   delete p;
 }
@@ -79,6 +81,68 @@ static bool gauss_taps(double fwhm, double delta, GaussTaps &t) {
   }
   for (int k = 0; k < 2 * kGaussMaxR + 1; ++k) t.w[k] = k <= 2 * t.R ? (float)(w[k] / sum) : 0.f;
   return true;
+}
+
+// Truncated-Gaussian TOF weight of a sample at signed distance d from a bin centre: the
+// mass of N(0, sigma^2) truncated to +-3 sigma (renormalised) inside [d - w/2, d + w/2].
+static double tof_F(double d, double sigma, double w) {
+  const double amax = 3.0 / sqrt(2.0);
+  double uhi = (0.5 * w - d) / (sqrt(2.0) * sigma), ulo = (-0.5 * w - d) / (sqrt(2.0) * sigma);
+  uhi = std::min(amax, std::max(-amax, uhi));
+  ulo = std::min(amax, std::max(-amax, ulo));
+  return (erf(uhi) - erf(ulo)) / (2.0 * erf(amax));
+}
+
+// Tables of the windowed TOF kernel: F sampled at nodes -R + k h (h = w / kTofM, R =
+// 3 sigma + w/2, k = 0..Ktab with Ktab = ceil(2R/h)), stored by window rows: row j of
+// the window of a sample whose node index for its lowest bin is ib = row + Ktab - kTofM
+// holds (F(ib - j M), F(ib - j M + 1) - F(ib - j M)).  The rows are padded to the
+// kernel's even WIN (4, 6 or 8).  Also the pairs of consecutive planes with equal axial
+// slope (two planes per thread share their TOF weights).
+static pet_status build_tof_window(pet_plan *pl, const std::vector<float4> &plane) {
+  const pet_geometry &g = pl->g;
+  DevPlan &dp = pl->dp;
+  const double w = g.tof_bin, sigma = g.tof_sigma;
+  const double R = 3.0 * sigma + 0.5 * w, h = w / kTofM;
+  const long long Ktab = (long long)ceil(2.0 * R / h);
+  const int win = (int)((Ktab - 1) / kTofM) + 1;
+  dp.tofw_win = win;
+  if (win > 8) return PET_OK;  // too many bins per sample for the register window
+  const int wk = win <= 4 ? 4 : (win <= 6 ? 6 : 8);
+  const double c0 = -0.5 * (pl->T - 1) * w;
+  dp.tofw_inv_h = (float)(1.0 / h);
+  dp.tofw_off = (float)((R - c0) / h - (double)Ktab + kTofM);
+  std::vector<float4> tab((size_t)kTofM * (wk / 2));
+  for (int row = 0; row < kTofM; ++row) {
+    const long long ib = row + Ktab - kTofM;
+    float f2[8 * 2];
+    for (int j = 0; j < wk; ++j) {
+      const long long kn = ib - (long long)j * kTofM;
+      const double a = tof_F(-R + kn * h, sigma, w), b = tof_F(-R + (kn + 1) * h, sigma, w);
+      f2[2 * j] = (float)a;
+      f2[2 * j + 1] = (float)(b - a);
+    }
+    for (int q = 0; q < wk / 2; ++q)
+      tab[(size_t)row * (wk / 2) + q] = make_float4(f2[4 * q], f2[4 * q + 1], f2[4 * q + 2], f2[4 * q + 3]);
+  }
+  std::vector<int> grp;
+  const int P = g.nplane;
+  for (int p = 0; p < P;) {
+    if (p + 1 < P && plane[p + 1].z == plane[p].z) {
+      grp.push_back(p); grp.push_back(p + 1); p += 2;
+    } else {
+      grp.push_back(p); grp.push_back(-1); p += 1;
+    }
+  }
+  if (dalloc(&pl->d_tofw_tab, tab.size()) != cudaSuccess || dalloc(&pl->d_tof_grp2, grp.size()) != cudaSuccess)
+    return PET_ERR_NOMEM;
+  if (cudaMemcpy(pl->d_tofw_tab, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(pl->d_tof_grp2, grp.data(), grp.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+    return PET_ERR_CUDA;
+  dp.tofw_tab = pl->d_tofw_tab;
+  dp.tof_grp2 = pl->d_tof_grp2;
+  dp.tof_ngrp2 = (int)(grp.size() / 2);
+  return tofk_init_device() == cudaSuccess ? PET_OK : PET_ERR_CUDA;
 }
 
 extern "C" pet_status pet_plan_create(const pet_geometry *geom, pet_plan **out) {
@@ -162,8 +226,6 @@ extern "C" pet_status pet_plan_create(const pet_geometry *geom, pet_plan **out) 
     dp.tof_erfc_amax = (float)erfc(amax);
     dp.tof_half_norm = (float)(1.0 / (2.0 * erf(amax)));
     dp.erfc_scale = (float)(kErfcTab / amax);
-    dp.tof_inv_w = (float)(1.0 / g.tof_bin);
-    dp.tof_reach = (float)(3.0 * g.tof_sigma / g.tof_bin);
   }
   // any fused-gradient launch (up to 16 parts per LOR) has at most this many blocks
   const int gb_all = (int)((16 * nlor + kBlock - 1) / kBlock) + 1;
@@ -204,6 +266,10 @@ extern "C" pet_status pet_plan_create(const pet_geometry *geom, pet_plan **out) 
     }
     dp.erfc_tab = pl->d_erfc_tab;
     dp.tof_erfc_amax = tab[kErfcTab];
+  }
+  if (pl->T > 1 && pl->T <= kTofMaxBins) {
+    pet_status e = build_tof_window(pl, plane);
+    if (e != PET_OK) { plan_free(pl); return e; }
   }
   {
     // plane groups by axial slope, sorted by axial centre (deterministic backprojector)
@@ -458,7 +524,7 @@ extern "C" pet_status pet_nrmse(const float *x, const float *ref, const uint8_t 
 extern "C" pet_status pet_plan_set_grad_shape(pet_plan *plan, int planes_per_thread, int parts) {
   if (!plan) return PET_ERR_ARG;
   const bool kok = planes_per_thread == 0 || planes_per_thread == 1 ||
-                   ((planes_per_thread == 2 || planes_per_thread == 4) && plan->T == 1);
+                   ((planes_per_thread == 2 || planes_per_thread == 4) && planes_per_thread <= max_planes(plan->dp));
   const bool sok = parts == 0 || ((parts == 1 || parts == 2 || parts == 4 || parts == 8 || parts == 16) &&
                                    parts <= max_split(plan->dp));
   if (!kok || !sok) return PET_ERR_ARG;
@@ -494,7 +560,7 @@ extern "C" pet_status pet_plan_autotune(pet_plan *plan, void *stream, int *plane
   for (int round = 0; round < 2; ++round)
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 5; ++b) {
-      if ((ks[a] > 1 && plan->T > 1) || ss[b] > max_split(plan->dp)) continue;
+      if (ks[a] > max_planes(plan->dp) || ss[b] > max_split(plan->dp)) continue;
       plan->dp.grad_k = ks[a];
       plan->dp.grad_split = ss[b];
       float ms = 0.f;

@@ -43,13 +43,26 @@ struct DevPlan {
   float tof_erfc_amax;  // erfc(amax)
   float tof_half_norm;  // 1 / (2 erf(amax))
   int *err;             // device error word (bit 0: infeasible ybar)
-  float tof_inv_w;       // 1 / bin width
-  float tof_reach;       // 3 sigma / bin width
   const float *erfc_tab; // erfc(j amax / kErfcTab), j = 0..kErfcTab (TOF)
   float erfc_scale;      // kErfcTab / amax
-  int grad_k;           // fused gradient: planes per thread (non-TOF; 0 = heuristic)
+  int grad_k;           // fused gradient: planes per thread (0 = heuristic)
   int grad_split;       // fused gradient: parts per LOR (0 = heuristic)
+  // windowed TOF kernel (tof_kernels.cu): rows of the interpolated bin-weight table,
+  // x' = t' / h + tofw_off is the window coordinate of a sample at (mirrored) position t'
+  const float4 *tofw_tab;  // [kTofM][tofw_win/2 padded to the kernel's WIN/2] (a, slope) pairs
+  float tofw_inv_h;        // 1 / h, h = bin width / kTofM
+  float tofw_off;          // (R - c_0)/h - Ktab + kTofM
+  int tofw_win;            // bins a sample can meet (0: no table)
+  const int *tof_grp2;     // [tof_ngrp2][2] plane pairs of equal axial slope (-1: none)
+  int tof_ngrp2;
 };
+
+// Windowed TOF kernel constants: threads per block, table rows per bin width (a power of
+// two), largest number of TOF bins.
+constexpr int kTofBlock = 512;
+constexpr int kTofLogM = 10;
+constexpr int kTofM = 1 << kTofLogM;
+constexpr int kTofMaxBins = 16;
 
 // Per-view data for the voxel-driven (deterministic) backprojector: fb0 is affine in
 // the radial index, fb0(v, r) ~ fbA + r fbB, used only to find candidate LORs.
@@ -208,13 +221,15 @@ cudaError_t launch_ratio(const DevPlan &P, int subset, const float *ax, float *q
 // q = m (1 - y/ybar); MODE_EM: q = m y/ybar; MODE_OBJ: no backprojection; MODE_SENS:
 // q = m (backprojects ones).  kl_part: per-block FP64 partial sums of the KL term
 // (may be NULL).  subset_dev (may be NULL) overrides `subset` from device memory.
-// Largest parts per LOR the fused gradient supports for this plan (16 non-TOF, 8 for
-// 11 or 13 TOF bins, else 4).
-int max_split(const DevPlan &P);
 cudaError_t launch_grad(const DevPlan &P, int subset, const int *subset_dev, const float *x,
                         const float *xT, float *g, float *gT, double *kl_part, int mode,
                         int *nblocks_out, cudaStream_t st);
 int grad_blocks(const DevPlan &P, int max_views);
+// Largest parts per LOR (16 without TOF, 8 with the windowed TOF kernel, else 4) and
+// planes per thread (4 without TOF, 2 with the windowed TOF kernel, else 1) of the fused
+// gradient for this plan.
+int max_split(const DevPlan &P);
+int max_planes(const DevPlan &P);
 cudaError_t launch_fill(float *p, size_t n, float v, cudaStream_t st);
 
 // One reconstruction of a batch, as seen by the batched fused-gradient kernel.
@@ -228,6 +243,16 @@ struct GradJob {
 cudaError_t launch_grad_batch(const GradJob *jobs, const int *begin, int njobs, int total_blocks, int K,
                               int split, cudaStream_t st);
 int grad_blocks_shape(const DevPlan &P, int nv, int K, int split);
+// Windowed TOF fused gradient (tof_kernels.cu): usable for this plan with K planes per
+// thread (1 or 2)?  Blocks of a launch over nv views, and the launch itself.
+bool tofk_supported(const DevPlan &P, int K);
+// Sets the dynamic shared-memory limits of the windowed TOF kernels on the current device
+// (called when a plan that uses them is created, outside any stream capture).
+cudaError_t tofk_init_device();
+int tofk_blocks(const DevPlan &P, int nv, int K, int split);
+cudaError_t launch_grad_tofk(const DevPlan &P, int K, int split, unsigned grid, int subset, const int *subset_dev,
+                             const float *x, const float *xT, float *g, float *gT, double *kl_part, int mode,
+                             cudaStream_t st);
 cudaError_t launch_transpose(const float *src, float *dst, int nx, int ny, int nz, int to_xfast,
                              int accumulate, cudaStream_t st);
 cudaError_t launch_mult(const DevPlan &P, const float *mu, const float *muT, const float *sens,

@@ -22,6 +22,8 @@ struct pet_plan {
   float *d_gzd = nullptr, *d_gzs = nullptr;
   int *d_gplane = nullptr;
   float *d_erfc_tab = nullptr;  // TOF: erfc table
+  float4 *d_tofw_tab = nullptr; // TOF: rows of the interpolated bin-weight table (windowed kernel)
+  int *d_tof_grp2 = nullptr;    // TOF: plane pairs of equal axial slope
   // derived data
   float *d_m = nullptr;         // [V][P][R] multiplicative factors
   float *d_sens = nullptr;      // [N] A^T 1

@@ -122,95 +122,6 @@ __device__ __forceinline__ void back_lor(const DevPlan &P, const Lor &L, float *
   }
 }
 
-// TOF with a window of bin edges: the per-thread bin accumulators live in shared
-// memory (column threadIdx.x of [TT][kBlock] arrays) so that a sample touches only the
-// bins that meet [t - 3 sigma, t + 3 sigma]: with kt = (t - e0)/w, bins
-// floor(kt - reach - m) ... floor(kt + reach + m), reach = 3 sigma / w, i.e. edges klo ..
-// khi.  The margin m = 1/64 bin (0.5 mm at 31 mm bins) exceeds the FP32 error of kt by
-// four orders of magnitude, so every bin left out has both edges clamped on the same
-// side and weight exactly zero.  Samples whose interpolated value is exactly zero
-// contribute nothing and skip the TOF work.
-__device__ __forceinline__ void tof_window(const DevPlan &P, float t, int T, int &klo, int &khi) {
-  constexpr float m = 1.f / 64.f;
-  const float kt = (t - P.tof_e0) * P.tof_inv_w;
-  klo = max(0, (int)floorf(fmaxf(kt - P.tof_reach - m, -4.f)));
-  khi = min(T, (int)floorf(fminf(kt + P.tof_reach + m, (float)T + 4.f)) + 1);
-}
-
-template <int TT, int STRIDE>
-__device__ __forceinline__ void forward_lor_tofw(const DevPlan &P, const Lor &L, const float *__restrict__ img,
-                                                 float *s_acc, float *s_cmp, bool act, int off,
-                                                 const float *tab) {
-  const int Na = L.xdrive ? P.nx : P.ny;
-  const int Nb = L.xdrive ? P.ny : P.nx;
-  const int plane = Na * Nb;
-  const int T = tof_bins<TT>(P);
-  const int tid = threadIdx.x;
-#pragma unroll
-  for (int b = 0; b < TT; ++b) {
-    s_acc[b * kBlock + tid] = 0.f;
-    s_cmp[b * kBlock + tid] = 0.f;
-  }
-  const float du = P.tof_w * P.tof_inv;
-  for (int i = L.i0 + off; i <= L.i1; i += STRIDE) {
-    if (!act || i >= Na) continue;
-    Samp S;
-    sample_at(L, i, Na, Nb, P.nz, S);
-    const float val = bilinear(img, S, plane);
-    if (val == 0.f) continue;
-    const float t = fmaf((float)i, L.dt, L.t0);
-    int klo, khi;
-    tof_window(P, t, T, klo, khi);
-    const float u0 = (P.tof_e0 - t) * P.tof_inv;
-    float uprev = fmaf((float)klo, du, u0);
-    float Gprev = tof_edge_G(P, tab, uprev);
-    for (int k = klo + 1; k <= khi; ++k) {
-      const float u = fmaf((float)k, du, u0);
-      const float G = tof_edge_G(P, tab, u);
-      const float w = tof_bin_weight(P, uprev, Gprev, u, G);
-      const int idx = (k - 1) * kBlock + tid;
-      float sum = s_acc[idx], c = s_cmp[idx];
-      kahan_add(sum, c, val * w);
-      s_acc[idx] = sum;
-      s_cmp[idx] = c;
-      uprev = u;
-      Gprev = G;
-    }
-  }
-}
-
-// Back: scatter sum_b q_b w_b(t) with q_b in shared memory (column threadIdx.x).
-template <int TT, int STRIDE>
-__device__ __forceinline__ void back_lor_tofw(const DevPlan &P, const Lor &L, float *__restrict__ img,
-                                              const float *s_q, bool act, int off, const float *tab) {
-  const int Na = L.xdrive ? P.nx : P.ny;
-  const int Nb = L.xdrive ? P.ny : P.nx;
-  const int plane = Na * Nb;
-  const int T = tof_bins<TT>(P);
-  const int tid = threadIdx.x;
-  const float du = P.tof_w * P.tof_inv;
-  for (int i = L.i0 + off; i <= L.i1; i += STRIDE) {
-    if (!act || i >= Na) continue;
-    Samp S;
-    sample_at(L, i, Na, Nb, P.nz, S);
-    const float t = fmaf((float)i, L.dt, L.t0);
-    int klo, khi;
-    tof_window(P, t, T, klo, khi);
-    const float u0 = (P.tof_e0 - t) * P.tof_inv;
-    float uprev = fmaf((float)klo, du, u0);
-    float Gprev = tof_edge_G(P, tab, uprev);
-    float val = 0.f;
-    for (int k = klo + 1; k <= khi; ++k) {
-      const float u = fmaf((float)k, du, u0);
-      const float G = tof_edge_G(P, tab, u);
-      val = fmaf(s_q[(k - 1) * kBlock + tid], tof_bin_weight(P, uprev, Gprev, u, G), val);
-      uprev = u;
-      Gprev = G;
-    }
-    if (val != 0.f) scatter(img, S, plane, val);
-  }
-}
-
 struct LorIdx {
   int v, p, r, l;
   bool ok;
@@ -647,83 +558,6 @@ __global__ void k_transpose(float *__restrict__ src, float *__restrict__ dst, in
   }
 }
 
-// Fused subset gradient for TOF (11 or 13 bins: the shared accumulators and the erfc
-// table must fit the 48 KB of static shared memory) with windowed bin edges (see
-// forward_lor_tofw); parts (SPLIT) interleave the planes as in k_grad and their partial
-// bin sums are combined in a fixed order through the shared accumulators.
-template <int TT, int SPLIT>
-__global__ void __launch_bounds__(kBlock) k_grad_tofw(DevPlan P, int subset, const int *subset_dev,
-                                                      const float *__restrict__ x, const float *__restrict__ xT,
-                                                      float *__restrict__ g, float *__restrict__ gT,
-                                                      double *__restrict__ kl_part, int mode) {
-  constexpr int LPB = kBlock / SPLIT;
-  __shared__ float s_tab[kErfcTab + 1];
-  __shared__ float s_acc[TT * kBlock];
-  __shared__ float s_cmp[TT * kBlock];
-  load_erfc_tab(P, s_tab);
-  if (subset_dev) subset = *subset_dev;
-  const int part = threadIdx.x / LPB;
-  const int tl = threadIdx.x % LPB;
-  const LorIdx id = lor_index(P, subset, (long long)blockIdx.x * LPB + tl);
-  double kl = 0.0;
-  Lor L = {};
-  if (id.ok) lor_setup(P, id.v, id.p, id.r, L);
-  warp_uniform_range(L, id.ok);
-  const int T = tof_bins<TT>(P);
-  float acc[TT];
-  if (mode != MODE_SENS) {
-    forward_lor_tofw<TT, SPLIT>(P, L, L.xdrive ? xT : x, s_acc, s_cmp, id.ok, part, s_tab);
-    if (SPLIT > 1) __syncthreads();
-#pragma unroll
-    for (int b = 0; b < TT; ++b) {
-      float t = 0.f;
-      if (b < T) {
-        t = s_acc[b * kBlock + tl];
-#pragma unroll
-        for (int j = 1; j < SPLIT; ++j) t += s_acc[b * kBlock + j * LPB + tl];
-      }
-      acc[b] = t;
-    }
-    if (SPLIT > 1) __syncthreads();  // every part has read the sums before q overwrites them
-  }
-  bool any = false;
-  {
-    const size_t lor = id.ok ? ((size_t)id.v * P.nplane + id.p) * P.nrad + id.r : 0;
-    const float mL = id.ok ? __ldg(&P.m[lor]) * L.L : 0.f;
-#pragma unroll
-    for (int b = 0; b < TT; ++b) {
-      float qb = 0.f;
-      if (b < T && id.ok) {
-        if (mode == MODE_SENS) {
-          qb = mL;
-        } else {
-          const size_t bi = lor * T + b;
-          const float ybar = fmaf(mL, acc[b], __ldg(&P.r[bi]));
-          const float yb = load_y(P, bi);
-          const bool count = kl_part && part == 0;
-          if (!(ybar > 0.f)) {
-            if (yb > 0.f) atomicOr(P.err, 1);
-            qb = (grad_like(mode) && yb == 0.f) ? mL : 0.f;
-            if (count && yb == 0.f) kl += (double)fmaxf(ybar, 0.f);
-          } else {
-            if (grad_like(mode)) qb = mL * (1.f - yb / ybar);
-            else if (mode == MODE_EM) qb = mL * (yb / ybar);
-            if (count) {
-              const double db = ybar, dy = yb;
-              kl += (yb > 0.f) ? (db - dy + dy * log(dy / db)) : db;
-            }
-          }
-        }
-        if (mode == MODE_NGRAD) qb = -qb;
-        any |= qb != 0.f;
-      }
-      if (b < T) s_acc[b * kBlock + threadIdx.x] = qb;
-    }
-  }
-  if (mode != MODE_OBJ) back_lor_tofw<TT, SPLIT>(P, L, L.xdrive ? gT : g, s_acc, any, part, s_tab);
-  if (kl_part) block_sum_store(kl, kl_part + blockIdx.x);
-}
-
 // Voxel-driven deterministic backprojection: each thread gathers, in a fixed order
 // with compensated summation, every (LOR, sample) whose bilinear footprint covers its
 // voxel.  The sample positions are computed with exactly the arithmetic of
@@ -859,6 +693,10 @@ __global__ void k_fill(float *__restrict__ p, size_t n, float v) {
 }
 
 // ----------------------------------------------------------------- launchers
+// TOF plans with a register window use the windowed kernel (tof_kernels.cu: 1 or 2 planes
+// per thread, up to 8 parts); other TOF plans the kernels with per-edge weights.
+static bool use_tofk(const DevPlan &P) { return P.T > 1 && tofk_supported(P, 1); }
+
 cudaError_t launch_fill(float *p, size_t n, float v, cudaStream_t st) {
   note_launch();
   k_fill<<<(unsigned)std::min<size_t>(2432, (n + 255) / 256), 256, 0, st>>>(p, n, v);
@@ -916,8 +754,6 @@ int grad_blocks(const DevPlan &P, int max_views) { return grad_blocks_for(P, max
 #define PET_GRAD_LAUNCH(SPLIT)                                                                  \
   do {                                                                                         \
     if (P.T <= 1) k_grad<1, SPLIT><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);   \
-    else if (P.T == 11) k_grad_tofw<11, SPLIT><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode); \
-    else if (P.T == 13) k_grad_tofw<13, SPLIT><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode); \
     else if (P.T <= 16) k_grad<16, SPLIT><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode); \
     else k_grad<32, SPLIT><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);           \
   } while (0)
@@ -926,16 +762,29 @@ static int views_for_launch(const DevPlan &P, int subset, const int *subset_dev)
   return subset_dev ? (P.nview + P.nsub - 1) / P.nsub : views_in(P, subset);
 }
 
-// Launch shape of the fused gradient: planes per thread (non-TOF only) and parts per
-// LOR.  P.grad_k / P.grad_split hold the autotuner's choice (0: heuristic).
-// Largest parts per LOR of a launch: 16 without TOF, 8 for the windowed TOF kernels
-// (11 and 13 bins), 4 otherwise.
+// Launch shape of the fused gradient: planes per thread and parts per LOR.  P.grad_k /
+// P.grad_split hold the autotuner's choice (0: heuristic).  Largest parts per LOR of a
+// launch: 16 without TOF, 8 with the windowed TOF kernel, 4 otherwise.
 int max_split(const DevPlan &P) {
   if (P.T <= 1) return 16;
-  return (P.T == 11 || P.T == 13) ? 8 : 4;
+  return use_tofk(P) ? 8 : 4;
+}
+
+// Largest planes per thread of the fused gradient: 4 without TOF, 2 with the windowed
+// TOF kernel, else 1.
+int max_planes(const DevPlan &P) {
+  if (P.T <= 1) return 4;
+  return tofk_supported(P, 2) ? 2 : 1;
 }
 
 static void grad_shape(const DevPlan &P, long long nlor, int &K, int &split) {
+  if (use_tofk(P)) {
+    K = P.grad_k > 0 ? P.grad_k : 2;
+    if (!tofk_supported(P, K)) K = 1;
+    split = P.grad_split > 0 ? P.grad_split : 1;
+    split = std::min(split, 8);
+    return;
+  }
   K = (P.T <= 1 && P.grad_k > 0) ? P.grad_k : 1;
   split = P.grad_split > 0 ? P.grad_split : split_for(nlor);
   split = std::min(split, max_split(P));
@@ -945,6 +794,7 @@ int grad_blocks_for(const DevPlan &P, int nv) {
   const long long nlor = (long long)nv * P.nplane * P.nrad;
   int K, split;
   grad_shape(P, nlor, K, split);
+  if (use_tofk(P)) return tofk_blocks(P, nv, K, split);
   const long long units = (long long)nv * ((P.nplane + K - 1) / K) * P.nrad;
   const int lpb = kBlock / split;
   return (int)((units + lpb - 1) / lpb);
@@ -963,6 +813,7 @@ cudaError_t launch_grad(const DevPlan &P, int subset, const int *subset_dev, con
   const unsigned grid = (unsigned)grad_blocks_for(P, nv);
   if (nblocks_out) *nblocks_out = (int)grid;
   if (grid == 0) return cudaSuccess;
+  if (use_tofk(P)) return launch_grad_tofk(P, K, split, grid, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
   note_launch();
   if (K == 4) {
     if (split == 16) PET_GRAD_MP(4, 16);
@@ -979,9 +830,7 @@ cudaError_t launch_grad(const DevPlan &P, int subset, const int *subset_dev, con
   } else if (split == 16) {
     k_grad<1, 16><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
   } else if (split == 8) {
-    if (P.T <= 1) k_grad<1, 8><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
-    else if (P.T == 11) k_grad_tofw<11, 8><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
-    else k_grad_tofw<13, 8><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
+    k_grad<1, 8><<<grid, kBlock, 0, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
   } else if (split == 4) {
     PET_GRAD_LAUNCH(4);
   } else if (split == 2) {

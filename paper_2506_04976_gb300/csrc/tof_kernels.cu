@@ -1,0 +1,421 @@
+// Fused TOF subset gradient (eq. 5 with the KL data term of Sec. 1.2 and the TOF-weighted
+// Joseph projector) for sm_103a, built around a sliding window of TOF bins.
+//
+// A sample at position t along its LOR meets the bins b with |t - c_b| < R = 3 sigma + w/2
+// (the truncated-Gaussian weight of bin b is F(t - c_b), F even, zero beyond R), at most
+// WIN consecutive bins.  Along a LOR t moves monotonically, so each thread keeps the
+// WIN bins around its current sample in registers and retires the lowest bin when the
+// window moves past it (forward: its finished sum goes to shared memory; backward: the
+// next bin's q enters the window).  LORs whose t decreases along the driving axis are
+// traversed with t' = -t and mirrored bins b' = T-1-b (F is even and c_{T-1-b} = -c_b),
+// so every window slides upward.
+//
+// Weights: F is tabulated at the spacing h = w/M (M = 1024 per bin width) and
+// interpolated linearly.  With x = (t - c_0 + R)/h the node index of bin b is
+// floor(x) - b M, so every bin of the window shares the fraction of x and the table can
+// be stored by rows: row ridx holds (F(node), F(node+1) - F(node)) for the WIN bins of a
+// window, and one sample reads one row.  The interpolation error is below h^2/8 max|F''|
+// ~ 1e-7 (and h/4 times the slope jump, ~1.4e-6 absolute, at the four kinks of the
+// truncation, where F is ~1e-2 of its peak).
+//
+// Planes per thread (K = 2): the two LORs of one view and radial bin on consecutive planes
+// of equal axial slope (a plane group built on the host) share their in-plane sample
+// positions and their positions t along the LOR, hence the TOF weights of every sample.
+//
+// Parts (SPLIT): the driving planes of a LOR are interleaved over SPLIT threads; each
+// keeps its own window; the bin sums are combined in a fixed order with compensation.
+#include <climits>
+
+#include "pet_internal.cuh"
+
+namespace petgb {
+
+namespace {
+
+__device__ __forceinline__ void kahan(float &sum, float &c, float v) {
+  const float yk = v - c;
+  const float tk = sum + yk;
+  c = (tk - sum) - yk;
+  sum = tk;
+}
+
+__device__ __forceinline__ double block_sum_512(double v) {
+  __shared__ double red[kTofBlock / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (w == 0) {
+    s = lane < kTofBlock / 32 ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  return s;  // valid in thread 0
+}
+
+// Window coordinate of sample i: x' = xs0 + i dxs; u = floor(x') split into the window's
+// lowest bin (u >> log2 M) and the table row (u & (M-1)); f the shared fraction.  u is
+// clamped so that a window never starts more than 4 bins below 0 or beyond T + WIN + 4.
+struct WinPos {
+  int kb, row;
+  float f;
+};
+
+__device__ __forceinline__ WinPos win_pos(float xs, int umax) {
+  const float fu = floorf(xs);
+  int u = (int)fu;
+  u = min(max(u, -4 * kTofM), umax);
+  WinPos w;
+  w.kb = u >> kTofLogM;
+  w.row = u & (kTofM - 1);
+  w.f = xs - fu;
+  return w;
+}
+
+template <int WIN>
+__device__ __forceinline__ void win_weights(const float4 *__restrict__ tab, int row, float f, float (&w)[WIN]) {
+  const float4 *r = tab + row * (WIN / 2);
+#pragma unroll
+  for (int j = 0; j < WIN / 2; ++j) {
+    const float4 e = r[j];
+    w[2 * j] = fmaf(f, e.y, e.x);
+    w[2 * j + 1] = fmaf(f, e.w, e.z);
+  }
+}
+
+}  // namespace
+
+// Fused TOF gradient: forward (windowed TOF sums), KL ratio, backprojection.  Dynamic
+// shared memory: the weight table (kTofM x WIN float2) then the bin sums / ratios
+// s_acc[(k T + b) kTofBlock + tid].
+template <int K, int WIN, int SPLIT>
+__global__ void __launch_bounds__(kTofBlock, 2) k_grad_tofk(DevPlan P, int subset, const int *subset_dev,
+                                                            const float *__restrict__ x, const float *__restrict__ xT,
+                                                            float *__restrict__ g, float *__restrict__ gT,
+                                                            double *__restrict__ kl_part, int mode) {
+  constexpr int LPB = kTofBlock / SPLIT;  // LOR groups per block
+  extern __shared__ float4 s_dyn[];
+  float4 *s_tab = s_dyn;
+  float *s_acc = reinterpret_cast<float *>(s_dyn + kTofM * (WIN / 2));
+  const int tid = threadIdx.x;
+  for (int k = tid; k < kTofM * (WIN / 2); k += kTofBlock) s_tab[k] = __ldg(&P.tofw_tab[k]);
+  const int T = P.T;
+  for (int k = 0; k < K * T; ++k) s_acc[k * kTofBlock + tid] = 0.f;
+  if (subset_dev) subset = *subset_dev;
+  const int part = tid / LPB;
+  const int tl = tid % LPB;
+  const int nsub = subset < 0 ? 1 : P.nsub;
+  const int s0 = subset < 0 ? 0 : subset;
+  const int nv = (P.nview - s0 + nsub - 1) / nsub;
+  const int ngrp = K == 1 ? P.nplane : P.tof_ngrp2;
+  const long long uid = (long long)blockIdx.x * LPB + tl;
+  const bool ok = uid < (long long)nv * ngrp * P.nrad;
+  int v = 0, r = 0, grp = 0;
+  if (ok) {
+    r = (int)(uid % P.nrad);
+    const long long t = uid / P.nrad;
+    grp = (int)(t % ngrp);
+    v = s0 + (int)(t / ngrp) * nsub;
+  }
+  // shared in-plane geometry and the planes of the group
+  const float4 vw = __ldg(&P.view[v]);
+  const float4 vr = __ldg(&P.vr[v * P.nrad + r]);
+  const bool xdrive = vw.x != 0.f;
+  const float dfb = vw.y, dau = vw.z, fb0 = vr.x, t0b = vr.y, inv2h = vr.z;
+  const float g1 = dau * inv2h, g2 = t0b * inv2h;
+  const int Na = xdrive ? P.nx : P.ny;
+  const int Nb = xdrive ? P.ny : P.nx;
+  const int plane = Na * Nb;
+  int pk[K];
+  bool pv[K];
+  float fz0[K], dfz[K];
+  float sec = 1.f;
+  float lo_b = 0.f, hi_b = (float)(Na - 1);
+  clip_range(fb0, dfb, -1.f, (float)Nb, lo_b, hi_b);
+  float lo = 1e30f, hi = -1e30f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int p = K == 1 ? grp : __ldg(&P.tof_grp2[2 * grp + k]);
+    pv[k] = ok && p >= 0;
+    pk[k] = pv[k] ? p : 0;
+    const float4 pl = __ldg(&P.plane[pk[k]]);
+    dfz[k] = g1 * pl.y;
+    fz0[k] = fmaf(g2, pl.y, pl.x);
+    if (k == 0) {  // planes of a group share their axial slope, hence sec and t
+      const float kk = pl.z * inv2h;
+      sec = sqrtf(fmaf(kk, kk, 1.f));
+    }
+    float lk = lo_b, hk = hi_b;
+    clip_range(fz0[k], dfz[k], -1.f, (float)P.nz, lk, hk);
+    if (pv[k] && lk <= hk) { lo = fminf(lo, lk); hi = fmaxf(hi, hk); }
+  }
+  Lor L = {};
+  if (lo <= hi) {
+    lo = fmaxf(lo, -2.f);
+    hi = fminf(hi, (float)Na + 1.f);
+    L.i0 = max(0, (int)floorf(lo) - 1);
+    L.i1 = min(Na - 1, (int)ceilf(hi) + 1);
+  } else {
+    L.i0 = 1;
+    L.i1 = 0;
+  }
+  warp_uniform_range(L, ok);
+  const float *img = xdrive ? xT : x;
+  // window coordinate along the (possibly mirrored) LOR
+  const bool mirror = dau < 0.f;
+  const float sg = mirror ? -1.f : 1.f;
+  const float xs0 = fmaf(sg * t0b * sec, P.tofw_inv_h, P.tofw_off);
+  const float dxs = sg * dau * sec * P.tofw_inv_h;
+  const int umax = (T + WIN + 4) * kTofM;
+  __syncthreads();  // table and cleared sums ready
+
+  if (mode != MODE_SENS) {
+    float acc[K][WIN];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int j = 0; j < WIN; ++j) acc[k][j] = 0.f;
+    int kbase = INT_MIN;
+    for (int i = L.i0 + part; i <= L.i1; i += SPLIT) {
+      if (!ok || i >= Na) continue;
+      const float fb = fmaf((float)i, dfb, fb0);
+      const float fbf = floorf(fb);
+      const int ib = (int)fbf;
+      const float wb = fb - fbf;
+      const bool b0 = (unsigned)ib < (unsigned)Nb;
+      const bool b1 = (unsigned)(ib + 1) < (unsigned)Nb && wb != 0.f;
+      const int row = i * Nb + ib;
+      float val[K];
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float fz = fmaf((float)i, dfz[k], fz0[k]);
+        const float fzf = floorf(fz);
+        const int iz = (int)fzf;
+        const float wz = fz - fzf;
+        const bool z0 = pv[k] && (unsigned)iz < (unsigned)P.nz;
+        const bool z1 = pv[k] && (unsigned)(iz + 1) < (unsigned)P.nz && wz != 0.f;
+        const int base = iz * plane + row;
+        const float v00 = (z0 && b0) ? __ldg(img + base) : 0.f;
+        const float v01 = (z0 && b1) ? __ldg(img + base + 1) : 0.f;
+        const float v10 = (z1 && b0) ? __ldg(img + base + plane) : 0.f;
+        const float v11 = (z1 && b1) ? __ldg(img + base + plane + 1) : 0.f;
+        val[k] = (1.f - wz) * ((1.f - wb) * v00 + wb * v01) + wz * ((1.f - wb) * v10 + wb * v11);
+        any |= val[k] != 0.f;
+      }
+      if (!any) continue;
+      const WinPos wp = win_pos(fmaf((float)i, dxs, xs0), umax);
+      if (kbase == INT_MIN) kbase = wp.kb;
+      while (kbase < wp.kb) {  // retire the lowest bin of the window
+        const int b = mirror ? T - 1 - kbase : kbase;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          if ((unsigned)kbase < (unsigned)T) s_acc[(k * T + b) * kTofBlock + tid] = acc[k][0];
+#pragma unroll
+          for (int j = 0; j < WIN - 1; ++j) acc[k][j] = acc[k][j + 1];
+          acc[k][WIN - 1] = 0.f;
+        }
+        ++kbase;
+      }
+      float w[WIN];
+      win_weights<WIN>(s_tab, wp.row, wp.f, w);
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int j = 0; j < WIN; ++j) acc[k][j] = fmaf(val[k], w[j], acc[k][j]);
+    }
+    if (kbase != INT_MIN) {
+#pragma unroll
+      for (int j = 0; j < WIN; ++j) {
+        const int kb = kbase + j;
+        if ((unsigned)kb < (unsigned)T) {
+          const int b = mirror ? T - 1 - kb : kb;
+#pragma unroll
+          for (int k = 0; k < K; ++k) s_acc[(k * T + b) * kTofBlock + tid] = acc[k][j];
+        }
+      }
+    }
+  }
+  __syncthreads();  // every part's bin sums are in shared memory
+
+  // KL ratio: part p handles the bins b = p, p + SPLIT, ... of its LOR group; the parts'
+  // sums are added in a fixed order with compensation; q replaces the sum of part 0.
+  double kl = 0.0;
+  bool anyq = false;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (!pv[k]) continue;
+    const size_t lor = ((size_t)v * P.nplane + pk[k]) * P.nrad + r;
+    const float mL = __ldg(&P.m[lor]) * fabsf(dau) * sec;
+    for (int b = part; b < T; b += SPLIT) {
+      float* cell = s_acc + (k * T + b) * kTofBlock;
+      float q;
+      if (mode == MODE_SENS) {
+        q = mL;
+      } else {
+        float sum = cell[tl], c = 0.f;
+#pragma unroll
+        for (int j = 1; j < SPLIT; ++j) kahan(sum, c, cell[j * LPB + tl]);
+        const size_t bi = lor * T + b;
+        const float ybar = fmaf(mL, sum, __ldg(&P.r[bi]));
+        const float yb = load_y(P, bi);
+        if (!(ybar > 0.f)) {
+          if (yb > 0.f) atomicOr(P.err, 1);
+          q = (grad_like(mode) && yb == 0.f) ? mL : 0.f;
+          if (kl_part && yb == 0.f) kl += (double)fmaxf(ybar, 0.f);
+        } else {
+          q = grad_like(mode) ? mL * (1.f - yb / ybar) : (mode == MODE_EM ? mL * (yb / ybar) : 0.f);
+          if (kl_part) {
+            const double db = ybar, dy = yb;
+            kl += (yb > 0.f) ? (db - dy + dy * log(dy / db)) : db;
+          }
+        }
+        if (mode == MODE_NGRAD) q = -q;
+      }
+      cell[tl] = q;
+    }
+  }
+  __syncthreads();  // every q of the block is in place
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (pv[k])
+      for (int b = 0; b < T; ++b) anyq |= s_acc[(k * T + b) * kTofBlock + tl] != 0.f;
+
+  if (mode != MODE_OBJ) {
+    float *out = xdrive ? gT : g;
+    float qw[K][WIN];
+    int kbase = INT_MIN;
+    for (int i = L.i0 + part; i <= L.i1; i += SPLIT) {
+      if (!anyq || i >= Na) continue;
+      const WinPos wp = win_pos(fmaf((float)i, dxs, xs0), umax);
+      if (kbase == INT_MIN || kbase < wp.kb) {
+        kbase = wp.kb;  // (re)load the window's ratios; the window only moves upward
+#pragma unroll
+        for (int j = 0; j < WIN; ++j) {
+          const int kb = kbase + j;
+          const bool in = (unsigned)kb < (unsigned)T;
+          const int b = mirror ? T - 1 - kb : kb;
+#pragma unroll
+          for (int k = 0; k < K; ++k) qw[k][j] = in ? s_acc[(k * T + b) * kTofBlock + tl] : 0.f;
+        }
+      }
+      float w[WIN];
+      win_weights<WIN>(s_tab, wp.row, wp.f, w);
+      float val[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        float a = 0.f;
+#pragma unroll
+        for (int j = 0; j < WIN; ++j) a = fmaf(qw[k][j], w[j], a);
+        val[k] = a;
+      }
+      const float fb = fmaf((float)i, dfb, fb0);
+      const float fbf = floorf(fb);
+      const int ib = (int)fbf;
+      const float wb = fb - fbf;
+      const bool b0 = (unsigned)ib < (unsigned)Nb;
+      const bool b1 = (unsigned)(ib + 1) < (unsigned)Nb && wb != 0.f;
+      const int row = i * Nb + ib;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (val[k] == 0.f) continue;
+        const float fz = fmaf((float)i, dfz[k], fz0[k]);
+        const float fzf = floorf(fz);
+        const int iz = (int)fzf;
+        const float wz = fz - fzf;
+        const bool z0 = (unsigned)iz < (unsigned)P.nz;
+        const bool z1 = (unsigned)(iz + 1) < (unsigned)P.nz && wz != 0.f;
+        const int base = iz * plane + row;
+        const float a0 = (1.f - wz) * val[k], a1 = wz * val[k];
+        if (z0 && b0) atomicAdd(out + base, (1.f - wb) * a0);
+        if (z0 && b1) atomicAdd(out + base + 1, wb * a0);
+        if (z1 && b0) atomicAdd(out + base + plane, (1.f - wb) * a1);
+        if (z1 && b1) atomicAdd(out + base + plane + 1, wb * a1);
+      }
+    }
+  }
+  if (kl_part) {
+    const double s = block_sum_512(kl);
+    if (tid == 0) kl_part[blockIdx.x] = s;
+  }
+}
+
+bool tofk_supported(const DevPlan &P, int K) {
+  if (P.T <= 1 || P.T > kTofMaxBins || !P.tofw_tab) return false;
+  if (P.tofw_win < 1 || P.tofw_win > 8) return false;
+  return K == 1 || (K == 2 && P.tof_grp2);
+}
+
+int tofk_blocks(const DevPlan &P, int nv, int K, int split) {
+  const long long ngrp = K == 1 ? P.nplane : P.tof_ngrp2;
+  const long long units = (long long)nv * ngrp * P.nrad;
+  const int lpb = kTofBlock / split;
+  return (int)((units + lpb - 1) / lpb);
+}
+
+template <int K, int WIN, int SPLIT>
+static cudaError_t launch_tofk_t(const DevPlan &P, unsigned grid, int subset, const int *subset_dev, const float *x,
+                                 const float *xT, float *g, float *gT, double *kl_part, int mode, cudaStream_t st) {
+  const size_t smem = (size_t)kTofM * (WIN / 2) * sizeof(float4) + (size_t)K * P.T * kTofBlock * sizeof(float);
+  k_grad_tofk<K, WIN, SPLIT><<<grid, kTofBlock, smem, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
+  return cudaGetLastError();
+}
+
+// Raises the dynamic shared-memory limit of one kernel instance to what its largest
+// launch needs (the table plus 2 x 16 bins of sums per thread).
+template <int K, int WIN, int SPLIT>
+static cudaError_t tofk_attr() {
+  return cudaFuncSetAttribute(k_grad_tofk<K, WIN, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(kTofM * (WIN / 2) * sizeof(float4) + 2 * kTofMaxBins * kTofBlock * sizeof(float)));
+}
+
+template <int K, int WIN>
+static cudaError_t tofk_attr_w() {
+  cudaError_t e = tofk_attr<K, WIN, 1>();
+  if (e == cudaSuccess) e = tofk_attr<K, WIN, 2>();
+  if (e == cudaSuccess) e = tofk_attr<K, WIN, 4>();
+  if (e == cudaSuccess) e = tofk_attr<K, WIN, 8>();
+  return e;
+}
+
+cudaError_t tofk_init_device() {
+  cudaError_t e = tofk_attr_w<1, 4>();
+  if (e == cudaSuccess) e = tofk_attr_w<1, 6>();
+  if (e == cudaSuccess) e = tofk_attr_w<1, 8>();
+  if (e == cudaSuccess) e = tofk_attr_w<2, 4>();
+  if (e == cudaSuccess) e = tofk_attr_w<2, 6>();
+  if (e == cudaSuccess) e = tofk_attr_w<2, 8>();
+  return e;
+}
+
+template <int K, int WIN>
+static cudaError_t launch_tofk_w(const DevPlan &P, unsigned grid, int split, int subset, const int *subset_dev,
+                                 const float *x, const float *xT, float *g, float *gT, double *kl_part, int mode,
+                                 cudaStream_t st) {
+  switch (split) {
+    case 1: return launch_tofk_t<K, WIN, 1>(P, grid, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
+    case 2: return launch_tofk_t<K, WIN, 2>(P, grid, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
+    case 4: return launch_tofk_t<K, WIN, 4>(P, grid, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
+    default: return launch_tofk_t<K, WIN, 8>(P, grid, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
+  }
+}
+
+cudaError_t launch_grad_tofk(const DevPlan &P, int K, int split, unsigned grid, int subset, const int *subset_dev,
+                             const float *x, const float *xT, float *g, float *gT, double *kl_part, int mode,
+                             cudaStream_t st) {
+  note_launch();
+  const int win = P.tofw_win <= 4 ? 4 : (P.tofw_win <= 6 ? 6 : 8);
+  if (K == 2) {
+    if (win == 4) return launch_tofk_w<2, 4>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
+    if (win == 6) return launch_tofk_w<2, 6>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
+    return launch_tofk_w<2, 8>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
+  }
+  if (win == 4) return launch_tofk_w<1, 4>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
+  if (win == 6) return launch_tofk_w<1, 6>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
+  return launch_tofk_w<1, 8>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
+}
+
+}  // namespace petgb

@@ -60,7 +60,13 @@ def case(key):
         specs = {
             "c1": ("c1", {}),
             "3d": ("c2", dict(nx=40, nz=23, nrad=70, nview=36, nsub=6)),
+            # TOF bins over the 362 mm FOV diagonal with sigma 24.8 mm: 11 bins of 33 mm
+            # (a sample meets at most 6 bins), 13 of 28 mm (7) and 5 of 73 mm (4) run the
+            # windowed TOF kernel; 25 bins of 15 mm (11) the kernels with per-edge weights
             "tof": ("c3", dict(nx=40, nz=23, nrad=70, nview=36, nsub=6)),
+            "tof13": ("c3", dict(nx=40, nz=23, nrad=70, nview=36, nsub=6, ntof=13)),
+            "tof5": ("c3", dict(nx=40, nz=23, nrad=70, nview=36, nsub=6, ntof=5)),
+            "tof25": ("c3", dict(nx=40, nz=23, nrad=70, nview=36, nsub=6, ntof=25)),
         }
         name, over = specs[key]
         _CASES[key] = Case(name, **over)
@@ -85,7 +91,7 @@ def test_multiplicative_factors(key):
     _close(m_gpu, c.m)
 
 
-@pytest.mark.parametrize("key", ["c1", "3d", "tof"])
+@pytest.mark.parametrize("key", ["c1", "3d", "tof", "tof13", "tof5", "tof25"])
 @pytest.mark.parametrize("subset", [0, 3])
 def test_forward_projection(key, subset):
     c = case(key)
@@ -96,7 +102,7 @@ def test_forward_projection(key, subset):
         _close(ax[j], ref[j])
 
 
-@pytest.mark.parametrize("key", ["c1", "3d", "tof"])
+@pytest.mark.parametrize("key", ["c1", "3d", "tof", "tof13", "tof25"])
 @pytest.mark.parametrize("det", [False, True])
 def test_back_projection(key, det):
     c = case(key)
@@ -126,7 +132,7 @@ def test_sensitivity_images(key):
     _close(c.plan.sensitivity(1).cpu().numpy(), O.sensitivity(c.G, c.n, 1, c.m))
 
 
-@pytest.mark.parametrize("key", ["c1", "3d", "tof"])
+@pytest.mark.parametrize("key", ["c1", "3d", "tof", "tof13", "tof5", "tof25"])
 @pytest.mark.parametrize("det", [False, True])
 def test_subset_objective_and_gradient(key, det):
     c = case(key)
@@ -146,7 +152,7 @@ def test_subset_objective_and_gradient(key, det):
     c.plan.check()
 
 
-@pytest.mark.parametrize("key", ["c1", "tof"])
+@pytest.mark.parametrize("key", ["c1", "tof", "tof25"])
 def test_objective_only_matches(key):
     c = case(key)
     o1, _ = c.plan.objective_grad(c.xt, 0)
@@ -278,7 +284,7 @@ def test_preconditioner(key, kind):
     assert np.all(np.abs(D - ref) <= 2e-5 * np.abs(ref) + 1e-7 * np.abs(ref).max())
 
 
-@pytest.mark.parametrize("key", ["c1", "tof"])
+@pytest.mark.parametrize("key", ["c1", "tof", "tof25"])
 def test_em_update(key):
     c = case(key)
     x = c.xt.clone()
@@ -341,16 +347,17 @@ def test_y_zero_and_zero_image():
     assert abs(float(obj) - ref) <= 1e-5 * ref
 
 
-@pytest.mark.parametrize("key", ["c1", "3d", "tof"])
-@pytest.mark.parametrize("shape", [(1, 1), (1, 2), (1, 4), (1, 8), (1, 16), (2, 1), (2, 4), (2, 8), (2, 16),
+@pytest.mark.parametrize("key", ["c1", "3d", "tof", "tof13", "tof5", "tof25"])
+@pytest.mark.parametrize("shape", [(1, 1), (1, 2), (1, 4), (1, 8), (1, 16), (2, 1), (2, 2), (2, 4), (2, 8), (2, 16),
                                    (4, 1), (4, 2), (4, 4), (4, 8), (4, 16)])
 def test_grad_launch_shapes(key, shape):
     """Every launch shape of the fused gradient (planes per thread x parts per LOR)
     gives the oracle's subset objective and gradient."""
     c = case(key)
     k, parts = shape
-    if (k > 1 or parts > 8) and c.plan.T > 1:
-        pytest.skip("planes per thread > 1 and sixteen parts per LOR are non-TOF only")
+    windowed = key in ("tof", "tof13", "tof5")
+    if c.plan.T > 1 and (k > (2 if windowed else 1) or parts > (8 if windowed else 4)):
+        pytest.skip("not a launch shape of this TOF kernel")
     c.plan.set_grad_shape(k, parts)
     try:
         s = 3
