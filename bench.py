@@ -65,8 +65,10 @@ def parse():
     ap.add_argument("--workload", default="c5", choices=["c5", "c2"],
                     help="step mode: the workload of the headline line (the other one is added as a key)")
     ap.add_argument("--no-c2", action="store_true", help="step mode: skip the secondary c2 measurement")
-    ap.add_argument("--study-config", default="c1", choices=["c1", "c2", "c2s", "c2s16", "c3s"],
+    ap.add_argument("--study-config", default="c1", choices=["c1", "c2", "c2s", "c2s1", "c2s16", "c3s"],
                     help="study mode: workload with a converged reference image in tests/golden")
+    ap.add_argument("--study-nsub", type=int, default=0,
+                    help="study mode: number of subsets (0: the workload's own; Sec. 3.2 uses 27)")
     return ap.parse_args()
 
 
@@ -466,7 +468,7 @@ def run_study(args, pet, dev, max_epochs=1500):
     ref_path = os.path.join(ROOT, "tests", "golden", f"ref_{cfg}_seed0.npz")
     ref = np.load(ref_path)
     p = synth.make_problem(cfg, 0)
-    n = p["nsub"]
+    n = args.study_nsub or p["nsub"]  # the objective does not depend on n, so the reference holds
     plan = pet.Plan(p["geom"], n)
     y = p["y"].view(np.int16) if p["y"].dtype == np.uint16 else p["y"].astype(np.int32)
     plan.set_data(torch.from_numpy(y).to(dev), torch.from_numpy(p["r"]).to(dev),
@@ -477,7 +479,7 @@ def run_study(args, pet, dev, max_epochs=1500):
     mask = torch.from_numpy(p["mask"]).to(dev)
     bg = torch.from_numpy(p["bg"]).to(dev)
     x0 = torch.ones(plan.img_shape, device=dev)
-    for s in range(n):
+    for s in range(n):  # one OSEM epoch (Sec. 3.1)
         plan.em_update(x0, s)
     from paper_2506_04976_gb300.presets import petric_solver_kwargs
     marks = (5, 10, 20, 50, 100, 500)
