@@ -59,9 +59,10 @@ def parse():
                          "study: epochs to 1%% NRMSE over algorithm x preconditioner x tau0 (2D)")
     ap.add_argument("--shape", default="auto",
                     help="grad mode: 'auto' (autotuner) or 'K,S' planes per thread, parts per LOR")
-    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c5"],
-                    help="grad mode: c2 (non-TOF, 1e7 counts), c3 (11 TOF bins, 1e6 counts) or c5 "
-                         "(13 TOF bins, 1.34 G bins, generated on the device)")
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c5", "c5p"],
+                    help="grad mode: c2 (non-TOF, 1e7 counts), c3 (11 TOF bins, 1e6 counts), c5 "
+                         "(13 TOF bins, 1.34 G bins, generated on the device) or c5p (c5 with 50 views: "
+                         "2 views per subset, for profiler captures)")
     ap.add_argument("--workload", default="c5", choices=["c5", "c2"],
                     help="step mode: the workload of the headline line (the other one is added as a key)")
     ap.add_argument("--no-c2", action="store_true", help="step mode: skip the secondary c2 measurement")
@@ -194,8 +195,9 @@ def load_workload(cfg, seed, dev):
     device (its 1.34 G TOF bins do not fit the host generator), the others on the host."""
     import torch
     from paper_2506_04976_gb300 import synth
-    if cfg in ("c3", "c5"):
-        p = synth.make_problem_device(cfg, seed, device=dev)
+    if cfg in ("c3", "c5", "c5p"):
+        p = synth.make_problem_device(cfg, seed, device=dev) if cfg != "c5p" else \
+            synth.make_problem_device("c5", seed, device=dev, nview=50)
         dt = dict(y=p["y"], r=p["r"], sens=p["sens"], mu=torch.from_numpy(p["mu"].astype(np.float32)).to(dev))
     else:
         p = synth.make_problem(cfg, seed)
@@ -654,24 +656,38 @@ def run_grad_only(args, pet, dev):
     p, dt = load_workload(args.config, 0, dev)
     plan = pet.Plan(p["geom"], p["nsub"])
     plan.set_data(dt["y"], dt["r"], dt["mu"], dt["sens"])
-    if args.shape == "auto":
-        shape = plan.autotune()
-    else:
-        shape = tuple(int(v) for v in args.shape.split(","))
-        plan.set_grad_shape(*shape)
     x = torch.from_numpy(np.maximum(p["x_true"], 0.05 * p["x_true"].max()).astype(np.float32)).to(dev)
     gbuf = torch.empty_like(x)
-    for i in range(args.warmup):
-        plan.objective_grad(x, i % p["nsub"], g=gbuf, want_obj=False)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for i in range(args.steps):
-        plan.objective_grad(x, i % p["nsub"], g=gbuf, want_obj=False)
-    b.record()
-    torch.cuda.synchronize()
-    print(json.dumps({"mode": "grad", "config": args.config, "shape": list(shape),
-                      "ms_per_call": a.elapsed_time(b) / max(args.steps, 1)}))
+
+    def timed(shape):
+        if shape == "auto":
+            shape = plan.autotune()
+        else:
+            plan.set_grad_shape(*shape)
+        for i in range(args.warmup):
+            plan.objective_grad(x, i % p["nsub"], g=gbuf, want_obj=False)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for i in range(args.steps):
+            plan.objective_grad(x, i % p["nsub"], g=gbuf, want_obj=False)
+        b.record()
+        torch.cuda.synchronize()
+        return {"shape": list(shape), "ms_per_call": a.elapsed_time(b) / max(args.steps, 1)}
+
+    if args.shape == "all":  # every launch shape the plan accepts, then the autotuner's choice
+        rows = []
+        for k in (1, 2, 4):
+            for sp in (1, 2, 4, 8, 16):
+                try:
+                    rows.append(timed((k, sp)))
+                except pet.PetError:
+                    continue
+        rows.append(dict(timed("auto"), autotuned=True))
+        print(json.dumps({"mode": "grad", "config": args.config, "shapes": rows}))
+        return
+    r = timed("auto" if args.shape == "auto" else tuple(int(v) for v in args.shape.split(",")))
+    print(json.dumps({"mode": "grad", "config": args.config, **r}))
 
 
 def tof_window(geom):

@@ -112,9 +112,10 @@ const float *pet_plan_sensitivity(const pet_plan *plan, int subset);
 
 /* Launch shape of the fused subset-gradient kernel: planes per thread (LORs of one view
  * and radial bin on different planes share their in-plane sample positions: 1, 2 or 4
- * without TOF; 1 or 2 with TOF when a sample meets at most 8 TOF bins, i.e. (6 sigma +
- * w)/w <= 8 for bin width w, and ntof <= 16 (the windowed TOF kernel; the two planes of a
- * thread then have equal axial slope and share their TOF weights); else 1) and parts per
+ * without TOF; also 1, 2 or 4 with TOF when a sample meets at most 8 TOF bins, i.e.
+ * (6 sigma + w)/w <= 8 for bin width w, and ntof <= 16 (the windowed TOF kernel; the
+ * planes of a thread then have equal axial slope and share their TOF weights); else 1)
+ * and parts per
  * LOR (1, 2, 4, 8 or 16: interleaved sets of the driving planes of one LOR processed by
  * different threads; 16 only without TOF; 8 without TOF, with the windowed TOF kernel or
  * with 11 or 13 TOF bins; else up to 4).  0 selects the built-in heuristic.  Results are

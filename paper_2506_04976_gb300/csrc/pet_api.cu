@@ -63,6 +63,7 @@ static void plan_free(pet_plan *p) {
   cudaFree(p->d_erfc_tab);
   cudaFree(p->d_tofw_tab);
   cudaFree(p->d_tof_grp2);
+  cudaFree(p->d_tof_grp4);
   cudaFree(p->d_xs); cudaFree(p->d_rtmp);
   delete p;
 }
@@ -94,11 +95,12 @@ static double tof_F(double d, double sigma, double w) {
 }
 
 // Tables of the windowed TOF kernel: F sampled at nodes -R + k h (h = w / kTofM, R =
-// 3 sigma + w/2, k = 0..Ktab with Ktab = ceil(2R/h)), stored by window rows: row j of
-// the window of a sample whose node index for its lowest bin is ib = row + Ktab - kTofM
-// holds (F(ib - j M), F(ib - j M + 1) - F(ib - j M)).  The rows are padded to the
-// kernel's even WIN (4, 6 or 8).  Also the pairs of consecutive planes with equal axial
-// slope (two planes per thread share their TOF weights).
+// 3 sigma + w/2, k = 0..Ktab with Ktab = ceil(2R/h)), stored by window rows: for a sample
+// whose node index for its lowest bin is ib = row + Ktab - kTofM, window bin j has node
+// n_j = ib - j M, value F(n_j) and slope F(n_j + 1) - F(n_j); a row holds the bins in
+// pairs (F_2p, F_2p+1, slope_2p, slope_2p+1), padded to the kernel's even WIN (4, 6 or
+// 8).  Also the groups of 2 and 4 consecutive planes with equal axial slope (the planes
+// of a thread share their TOF weights).
 static pet_status build_tof_window(pet_plan *pl, const std::vector<float4> &plane) {
   const pet_geometry &g = pl->g;
   DevPlan &dp = pl->dp;
@@ -115,33 +117,41 @@ static pet_status build_tof_window(pet_plan *pl, const std::vector<float4> &plan
   std::vector<float4> tab((size_t)kTofM * (wk / 2));
   for (int row = 0; row < kTofM; ++row) {
     const long long ib = row + Ktab - kTofM;
-    float f2[8 * 2];
+    float fv[8], fs[8];
     for (int j = 0; j < wk; ++j) {
       const long long kn = ib - (long long)j * kTofM;
       const double a = tof_F(-R + kn * h, sigma, w), b = tof_F(-R + (kn + 1) * h, sigma, w);
-      f2[2 * j] = (float)a;
-      f2[2 * j + 1] = (float)(b - a);
+      fv[j] = (float)a;
+      fs[j] = (float)(b - a);
     }
     for (int q = 0; q < wk / 2; ++q)
-      tab[(size_t)row * (wk / 2) + q] = make_float4(f2[4 * q], f2[4 * q + 1], f2[4 * q + 2], f2[4 * q + 3]);
+      tab[(size_t)row * (wk / 2) + q] = make_float4(fv[2 * q], fv[2 * q + 1], fs[2 * q], fs[2 * q + 1]);
   }
-  std::vector<int> grp;
+  // groups of up to K consecutive planes of equal axial slope, padded with -1
   const int P = g.nplane;
-  for (int p = 0; p < P;) {
-    if (p + 1 < P && plane[p + 1].z == plane[p].z) {
-      grp.push_back(p); grp.push_back(p + 1); p += 2;
-    } else {
-      grp.push_back(p); grp.push_back(-1); p += 1;
+  auto groups = [&](int K) {
+    std::vector<int> grp;
+    for (int p = 0; p < P;) {
+      int c = 1;
+      while (c < K && p + c < P && plane[p + c].z == plane[p].z) ++c;
+      for (int k = 0; k < K; ++k) grp.push_back(k < c ? p + k : -1);
+      p += c;
     }
-  }
-  if (dalloc(&pl->d_tofw_tab, tab.size()) != cudaSuccess || dalloc(&pl->d_tof_grp2, grp.size()) != cudaSuccess)
+    return grp;
+  };
+  const std::vector<int> grp2 = groups(2), grp4 = groups(4);
+  if (dalloc(&pl->d_tofw_tab, tab.size()) != cudaSuccess || dalloc(&pl->d_tof_grp2, grp2.size()) != cudaSuccess ||
+      dalloc(&pl->d_tof_grp4, grp4.size()) != cudaSuccess)
     return PET_ERR_NOMEM;
   if (cudaMemcpy(pl->d_tofw_tab, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(pl->d_tof_grp2, grp.data(), grp.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+      cudaMemcpy(pl->d_tof_grp2, grp2.data(), grp2.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(pl->d_tof_grp4, grp4.data(), grp4.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
     return PET_ERR_CUDA;
   dp.tofw_tab = pl->d_tofw_tab;
   dp.tof_grp2 = pl->d_tof_grp2;
-  dp.tof_ngrp2 = (int)(grp.size() / 2);
+  dp.tof_ngrp2 = (int)(grp2.size() / 2);
+  dp.tof_grp4 = pl->d_tof_grp4;
+  dp.tof_ngrp4 = (int)(grp4.size() / 4);
   return tofk_init_device() == cudaSuccess ? PET_OK : PET_ERR_CUDA;
 }
 

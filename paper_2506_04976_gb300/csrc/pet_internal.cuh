@@ -49,12 +49,14 @@ struct DevPlan {
   int grad_split;       // fused gradient: parts per LOR (0 = heuristic)
   // windowed TOF kernel (tof_kernels.cu): rows of the interpolated bin-weight table,
   // x' = t' / h + tofw_off is the window coordinate of a sample at (mirrored) position t'
-  const float4 *tofw_tab;  // [kTofM][tofw_win/2 padded to the kernel's WIN/2] (a, slope) pairs
+  const float4 *tofw_tab;  // [kTofM][WIN/2] (F_2p, F_2p+1, slope_2p, slope_2p+1), WIN = 4, 6 or 8
   float tofw_inv_h;        // 1 / h, h = bin width / kTofM
   float tofw_off;          // (R - c_0)/h - Ktab + kTofM
   int tofw_win;            // bins a sample can meet (0: no table)
   const int *tof_grp2;     // [tof_ngrp2][2] plane pairs of equal axial slope (-1: none)
   int tof_ngrp2;
+  const int *tof_grp4;     // [tof_ngrp4][4] plane quadruples of equal axial slope (-1: none)
+  int tof_ngrp4;
 };
 
 // Windowed TOF kernel constants: threads per block, table rows per bin width (a power of
@@ -226,7 +228,7 @@ cudaError_t launch_grad(const DevPlan &P, int subset, const int *subset_dev, con
                         int *nblocks_out, cudaStream_t st);
 int grad_blocks(const DevPlan &P, int max_views);
 // Largest parts per LOR (16 without TOF, 8 with the windowed TOF kernel, else 4) and
-// planes per thread (4 without TOF, 2 with the windowed TOF kernel, else 1) of the fused
+// planes per thread (4 without TOF or with the windowed TOF kernel, else 1) of the fused
 // gradient for this plan.
 int max_split(const DevPlan &P);
 int max_planes(const DevPlan &P);
@@ -244,7 +246,7 @@ cudaError_t launch_grad_batch(const GradJob *jobs, const int *begin, int njobs, 
                               int split, cudaStream_t st);
 int grad_blocks_shape(const DevPlan &P, int nv, int K, int split);
 // Windowed TOF fused gradient (tof_kernels.cu): usable for this plan with K planes per
-// thread (1 or 2)?  Blocks of a launch over nv views, and the launch itself.
+// thread (1, 2 or 4)?  Blocks of a launch over nv views, and the launch itself.
 bool tofk_supported(const DevPlan &P, int K);
 // Sets the dynamic shared-memory limits of the windowed TOF kernels on the current device
 // (called when a plan that uses them is created, outside any stream capture).

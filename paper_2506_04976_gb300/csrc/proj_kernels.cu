@@ -774,7 +774,7 @@ int max_split(const DevPlan &P) {
 // TOF kernel, else 1.
 int max_planes(const DevPlan &P) {
   if (P.T <= 1) return 4;
-  return tofk_supported(P, 2) ? 2 : 1;
+  return tofk_supported(P, 4) ? 4 : (tofk_supported(P, 2) ? 2 : 1);
 }
 
 static void grad_shape(const DevPlan &P, long long nlor, int &K, int &split) {

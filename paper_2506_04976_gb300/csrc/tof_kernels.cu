@@ -13,17 +13,21 @@
 // Weights: F is tabulated at the spacing h = w/M (M = 1024 per bin width) and
 // interpolated linearly.  With x = (t - c_0 + R)/h the node index of bin b is
 // floor(x) - b M, so every bin of the window shares the fraction of x and the table can
-// be stored by rows: row ridx holds (F(node), F(node+1) - F(node)) for the WIN bins of a
-// window, and one sample reads one row.  The interpolation error is below h^2/8 max|F''|
-// ~ 1e-7 (and h/4 times the slope jump, ~1.4e-6 absolute, at the four kinks of the
-// truncation, where F is ~1e-2 of its peak).
+// be stored by rows: row ridx holds, for each pair of window bins (j, j+1), the values
+// (F(n_j), F(n_{j+1})) and slopes (F(n_j + 1) - F(n_j), ...) at their nodes n_j, and
+// one sample reads one row.  The interpolation error is below h^2/8 max|F''| ~ 1e-7
+// (and h/4 times the slope jump, ~1.4e-6 absolute, at the four kinks of the truncation,
+// where F is ~1e-2 of its peak).  Pairs of bins are evaluated with the packed FP32x2
+// FMA of sm_100+ (two independent round-to-nearest FMAs, the same results as two FFMAs).
 //
-// Planes per thread (K = 2): the two LORs of one view and radial bin on consecutive planes
-// of equal axial slope (a plane group built on the host) share their in-plane sample
+// Planes per thread (K = 2 or 4): LORs of one view and radial bin on consecutive planes
+// of equal axial slope (plane groups built on the host) share their in-plane sample
 // positions and their positions t along the LOR, hence the TOF weights of every sample.
 //
 // Parts (SPLIT): the driving planes of a LOR are interleaved over SPLIT threads; each
 // keeps its own window; the bin sums are combined in a fixed order with compensation.
+// With one part a thread owns its LORs from the forward sums to the backprojection, so
+// no block barrier separates the phases.
 #include <climits>
 
 #include "pet_internal.cuh"
@@ -39,8 +43,20 @@ __device__ __forceinline__ void kahan(float &sum, float &c, float v) {
   sum = tk;
 }
 
-__device__ __forceinline__ double block_sum_512(double v) {
-  __shared__ double red[kTofBlock / 32];
+// d = a * b + c on two lanes at once (fma.rn.f32x2).
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[NT / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -49,7 +65,7 @@ __device__ __forceinline__ double block_sum_512(double v) {
   __syncthreads();
   double s = 0.0;
   if (w == 0) {
-    s = lane < kTofBlock / 32 ? red[lane] : 0.0;
+    s = lane < NT / 32 ? red[lane] : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   }
@@ -75,42 +91,44 @@ __device__ __forceinline__ WinPos win_pos(float xs, int umax) {
   return w;
 }
 
+// Weights of the WIN window bins as WIN/2 pairs: w2[p] = (w_{2p}, w_{2p+1}).
 template <int WIN>
-__device__ __forceinline__ void win_weights(const float4 *__restrict__ tab, int row, float f, float (&w)[WIN]) {
+__device__ __forceinline__ void win_weights(const float4 *__restrict__ tab, int row, float f, float2 (&w2)[WIN / 2]) {
   const float4 *r = tab + row * (WIN / 2);
+  const float2 ff = make_float2(f, f);
 #pragma unroll
-  for (int j = 0; j < WIN / 2; ++j) {
-    const float4 e = r[j];
-    w[2 * j] = fmaf(f, e.y, e.x);
-    w[2 * j + 1] = fmaf(f, e.w, e.z);
+  for (int p = 0; p < WIN / 2; ++p) {
+    const float4 e = r[p];  // (F_2p, F_2p+1, slope_2p, slope_2p+1)
+    w2[p] = fma2(ff, make_float2(e.z, e.w), make_float2(e.x, e.y));
   }
 }
 
 }  // namespace
 
-// Fused TOF gradient: forward (windowed TOF sums), KL ratio, backprojection.  Dynamic
-// shared memory: the weight table (kTofM x WIN float2) then the bin sums / ratios
-// s_acc[(k T + b) kTofBlock + tid].
-template <int K, int WIN, int SPLIT>
-__global__ void __launch_bounds__(kTofBlock, 2) k_grad_tofk(DevPlan P, int subset, const int *subset_dev,
-                                                            const float *__restrict__ x, const float *__restrict__ xT,
-                                                            float *__restrict__ g, float *__restrict__ gT,
-                                                            double *__restrict__ kl_part, int mode) {
-  constexpr int LPB = kTofBlock / SPLIT;  // LOR groups per block
+// Fused TOF gradient: forward (windowed TOF sums), KL ratio, backprojection.  NT threads
+// per block; dynamic shared memory: the weight table (kTofM rows of WIN/2 float4) then the
+// bin sums / ratios s_acc[(k T + b) NT + tid].
+template <int K, int WIN, int SPLIT, int NT>
+__global__ void __launch_bounds__(NT, 2) k_grad_tofk(DevPlan P, int subset, const int *subset_dev,
+                                                             const float *__restrict__ x, const float *__restrict__ xT,
+                                                             float *__restrict__ g, float *__restrict__ gT,
+                                                             double *__restrict__ kl_part, int mode) {
+  constexpr int LPB = NT / SPLIT;  // LOR groups per block
+  constexpr int WP = WIN / 2;
   extern __shared__ float4 s_dyn[];
   float4 *s_tab = s_dyn;
-  float *s_acc = reinterpret_cast<float *>(s_dyn + kTofM * (WIN / 2));
+  float *s_acc = reinterpret_cast<float *>(s_dyn + kTofM * WP);
   const int tid = threadIdx.x;
-  for (int k = tid; k < kTofM * (WIN / 2); k += kTofBlock) s_tab[k] = __ldg(&P.tofw_tab[k]);
+  for (int k = tid; k < kTofM * WP; k += NT) s_tab[k] = __ldg(&P.tofw_tab[k]);
   const int T = P.T;
-  for (int k = 0; k < K * T; ++k) s_acc[k * kTofBlock + tid] = 0.f;
+  for (int k = 0; k < K * T; ++k) s_acc[k * NT + tid] = 0.f;
   if (subset_dev) subset = *subset_dev;
   const int part = tid / LPB;
   const int tl = tid % LPB;
   const int nsub = subset < 0 ? 1 : P.nsub;
   const int s0 = subset < 0 ? 0 : subset;
   const int nv = (P.nview - s0 + nsub - 1) / nsub;
-  const int ngrp = K == 1 ? P.nplane : P.tof_ngrp2;
+  const int ngrp = K == 1 ? P.nplane : (K == 2 ? P.tof_ngrp2 : P.tof_ngrp4);
   const long long uid = (long long)blockIdx.x * LPB + tl;
   const bool ok = uid < (long long)nv * ngrp * P.nrad;
   int v = 0, r = 0, grp = 0;
@@ -138,7 +156,7 @@ __global__ void __launch_bounds__(kTofBlock, 2) k_grad_tofk(DevPlan P, int subse
   float lo = 1e30f, hi = -1e30f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const int p = K == 1 ? grp : __ldg(&P.tof_grp2[2 * grp + k]);
+    const int p = K == 1 ? grp : __ldg(&(K == 2 ? P.tof_grp2 : P.tof_grp4)[K * grp + k]);
     pv[k] = ok && p >= 0;
     pk[k] = pv[k] ? p : 0;
     const float4 pl = __ldg(&P.plane[pk[k]]);
@@ -173,11 +191,11 @@ __global__ void __launch_bounds__(kTofBlock, 2) k_grad_tofk(DevPlan P, int subse
   __syncthreads();  // table and cleared sums ready
 
   if (mode != MODE_SENS) {
-    float acc[K][WIN];
+    float2 acc[K][WP];  // bins (2p, 2p+1) of the window for each plane
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
-      for (int j = 0; j < WIN; ++j) acc[k][j] = 0.f;
+      for (int q = 0; q < WP; ++q) acc[k][q] = make_float2(0.f, 0.f);
     int kbase = INT_MIN;
     for (int i = L.i0 + part; i <= L.i1; i += SPLIT) {
       if (!ok || i >= Na) continue;
@@ -209,23 +227,27 @@ __global__ void __launch_bounds__(kTofBlock, 2) k_grad_tofk(DevPlan P, int subse
       if (!any) continue;
       const WinPos wp = win_pos(fmaf((float)i, dxs, xs0), umax);
       if (kbase == INT_MIN) kbase = wp.kb;
-      while (kbase < wp.kb) {  // retire the lowest bin of the window
+      while (kbase < wp.kb) {  // retire the lowest bin of the window, shift the rest down
         const int b = mirror ? T - 1 - kbase : kbase;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-          if ((unsigned)kbase < (unsigned)T) s_acc[(k * T + b) * kTofBlock + tid] = acc[k][0];
+          if ((unsigned)kbase < (unsigned)T) s_acc[(k * T + b) * NT + tid] = acc[k][0].x;
 #pragma unroll
-          for (int j = 0; j < WIN - 1; ++j) acc[k][j] = acc[k][j + 1];
-          acc[k][WIN - 1] = 0.f;
+          for (int q = 0; q < WP; ++q) {
+            acc[k][q].x = acc[k][q].y;
+            acc[k][q].y = q + 1 < WP ? acc[k][q + 1].x : 0.f;
+          }
         }
         ++kbase;
       }
-      float w[WIN];
-      win_weights<WIN>(s_tab, wp.row, wp.f, w);
+      float2 w2[WP];
+      win_weights<WIN>(s_tab, wp.row, wp.f, w2);
 #pragma unroll
-      for (int k = 0; k < K; ++k)
+      for (int k = 0; k < K; ++k) {
+        const float2 vv = make_float2(val[k], val[k]);
 #pragma unroll
-        for (int j = 0; j < WIN; ++j) acc[k][j] = fmaf(val[k], w[j], acc[k][j]);
+        for (int q = 0; q < WP; ++q) acc[k][q] = fma2(vv, w2[q], acc[k][q]);
+      }
     }
     if (kbase != INT_MIN) {
 #pragma unroll
@@ -234,12 +256,12 @@ __global__ void __launch_bounds__(kTofBlock, 2) k_grad_tofk(DevPlan P, int subse
         if ((unsigned)kb < (unsigned)T) {
           const int b = mirror ? T - 1 - kb : kb;
 #pragma unroll
-          for (int k = 0; k < K; ++k) s_acc[(k * T + b) * kTofBlock + tid] = acc[k][j];
+          for (int k = 0; k < K; ++k) s_acc[(k * T + b) * NT + tid] = (j & 1) ? acc[k][j / 2].y : acc[k][j / 2].x;
         }
       }
     }
   }
-  __syncthreads();  // every part's bin sums are in shared memory
+  if (SPLIT > 1) __syncthreads();  // every part's bin sums are in shared memory
 
   // KL ratio: part p handles the bins b = p, p + SPLIT, ... of its LOR group; the parts'
   // sums are added in a fixed order with compensation; q replaces the sum of part 0.
@@ -251,7 +273,7 @@ __global__ void __launch_bounds__(kTofBlock, 2) k_grad_tofk(DevPlan P, int subse
     const size_t lor = ((size_t)v * P.nplane + pk[k]) * P.nrad + r;
     const float mL = __ldg(&P.m[lor]) * fabsf(dau) * sec;
     for (int b = part; b < T; b += SPLIT) {
-      float* cell = s_acc + (k * T + b) * kTofBlock;
+      float *cell = s_acc + (k * T + b) * NT;
       float q;
       if (mode == MODE_SENS) {
         q = mL;
@@ -276,17 +298,21 @@ __global__ void __launch_bounds__(kTofBlock, 2) k_grad_tofk(DevPlan P, int subse
         if (mode == MODE_NGRAD) q = -q;
       }
       cell[tl] = q;
+      anyq |= q != 0.f;
     }
   }
-  __syncthreads();  // every q of the block is in place
+  if (SPLIT > 1) {
+    __syncthreads();  // every q of the block is in place
+    anyq = false;
 #pragma unroll
-  for (int k = 0; k < K; ++k)
-    if (pv[k])
-      for (int b = 0; b < T; ++b) anyq |= s_acc[(k * T + b) * kTofBlock + tl] != 0.f;
+    for (int k = 0; k < K; ++k)
+      if (pv[k])
+        for (int b = 0; b < T; ++b) anyq |= s_acc[(k * T + b) * NT + tl] != 0.f;
+  }
 
   if (mode != MODE_OBJ) {
     float *out = xdrive ? gT : g;
-    float qw[K][WIN];
+    float2 qw[K][WP];
     int kbase = INT_MIN;
     for (int i = L.i0 + part; i <= L.i1; i += SPLIT) {
       if (!anyq || i >= Na) continue;
@@ -299,18 +325,22 @@ __global__ void __launch_bounds__(kTofBlock, 2) k_grad_tofk(DevPlan P, int subse
           const bool in = (unsigned)kb < (unsigned)T;
           const int b = mirror ? T - 1 - kb : kb;
 #pragma unroll
-          for (int k = 0; k < K; ++k) qw[k][j] = in ? s_acc[(k * T + b) * kTofBlock + tl] : 0.f;
+          for (int k = 0; k < K; ++k) {
+            const float qv = in ? s_acc[(k * T + b) * NT + tl] : 0.f;
+            if (j & 1) qw[k][j / 2].y = qv;
+            else qw[k][j / 2].x = qv;
+          }
         }
       }
-      float w[WIN];
-      win_weights<WIN>(s_tab, wp.row, wp.f, w);
+      float2 w2[WP];
+      win_weights<WIN>(s_tab, wp.row, wp.f, w2);
       float val[K];
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        float a = 0.f;
+        float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int j = 0; j < WIN; ++j) a = fmaf(qw[k][j], w[j], a);
-        val[k] = a;
+        for (int q = 0; q < WP; ++q) a = fma2(qw[k][q], w2[q], a);
+        val[k] = a.x + a.y;
       }
       const float fb = fmaf((float)i, dfb, fb0);
       const float fbf = floorf(fb);
@@ -338,38 +368,44 @@ __global__ void __launch_bounds__(kTofBlock, 2) k_grad_tofk(DevPlan P, int subse
     }
   }
   if (kl_part) {
-    const double s = block_sum_512(kl);
+    const double s = block_sum<NT>(kl);
     if (tid == 0) kl_part[blockIdx.x] = s;
   }
 }
 
+// Threads per block: 512 for 1 or 2 planes per thread, 256 for 4 (more registers).
+template <int K>
+constexpr int tofk_nt() { return K == 4 ? 256 : kTofBlock; }
+
 bool tofk_supported(const DevPlan &P, int K) {
   if (P.T <= 1 || P.T > kTofMaxBins || !P.tofw_tab) return false;
   if (P.tofw_win < 1 || P.tofw_win > 8) return false;
-  return K == 1 || (K == 2 && P.tof_grp2);
+  return K == 1 || (K == 2 && P.tof_grp2) || (K == 4 && P.tof_grp4);
 }
 
 int tofk_blocks(const DevPlan &P, int nv, int K, int split) {
-  const long long ngrp = K == 1 ? P.nplane : P.tof_ngrp2;
+  const long long ngrp = K == 1 ? P.nplane : (K == 2 ? P.tof_ngrp2 : P.tof_ngrp4);
   const long long units = (long long)nv * ngrp * P.nrad;
-  const int lpb = kTofBlock / split;
+  const int lpb = (K == 4 ? tofk_nt<4>() : kTofBlock) / split;
   return (int)((units + lpb - 1) / lpb);
 }
 
 template <int K, int WIN, int SPLIT>
 static cudaError_t launch_tofk_t(const DevPlan &P, unsigned grid, int subset, const int *subset_dev, const float *x,
                                  const float *xT, float *g, float *gT, double *kl_part, int mode, cudaStream_t st) {
-  const size_t smem = (size_t)kTofM * (WIN / 2) * sizeof(float4) + (size_t)K * P.T * kTofBlock * sizeof(float);
-  k_grad_tofk<K, WIN, SPLIT><<<grid, kTofBlock, smem, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
+  constexpr int NT = tofk_nt<K>();
+  const size_t smem = (size_t)kTofM * (WIN / 2) * sizeof(float4) + (size_t)K * P.T * NT * sizeof(float);
+  k_grad_tofk<K, WIN, SPLIT, NT><<<grid, NT, smem, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
   return cudaGetLastError();
 }
 
 // Raises the dynamic shared-memory limit of one kernel instance to what its largest
-// launch needs (the table plus 2 x 16 bins of sums per thread).
+// launch needs (the table plus K x 16 bins of sums per thread).
 template <int K, int WIN, int SPLIT>
 static cudaError_t tofk_attr() {
-  return cudaFuncSetAttribute(k_grad_tofk<K, WIN, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(kTofM * (WIN / 2) * sizeof(float4) + 2 * kTofMaxBins * kTofBlock * sizeof(float)));
+  constexpr int NT = tofk_nt<K>();
+  return cudaFuncSetAttribute(k_grad_tofk<K, WIN, SPLIT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(kTofM * (WIN / 2) * sizeof(float4) + K * kTofMaxBins * NT * sizeof(float)));
 }
 
 template <int K, int WIN>
@@ -382,12 +418,16 @@ static cudaError_t tofk_attr_w() {
 }
 
 cudaError_t tofk_init_device() {
-  cudaError_t e = tofk_attr_w<1, 4>();
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = tofk_attr_w<1, 4>();
   if (e == cudaSuccess) e = tofk_attr_w<1, 6>();
   if (e == cudaSuccess) e = tofk_attr_w<1, 8>();
   if (e == cudaSuccess) e = tofk_attr_w<2, 4>();
   if (e == cudaSuccess) e = tofk_attr_w<2, 6>();
   if (e == cudaSuccess) e = tofk_attr_w<2, 8>();
+  if (e == cudaSuccess) e = tofk_attr_w<4, 4>();
+  if (e == cudaSuccess) e = tofk_attr_w<4, 6>();
+  if (e == cudaSuccess) e = tofk_attr_w<4, 8>();
   return e;
 }
 
@@ -403,19 +443,23 @@ static cudaError_t launch_tofk_w(const DevPlan &P, unsigned grid, int split, int
   }
 }
 
+template <int K>
+static cudaError_t launch_tofk_k(const DevPlan &P, unsigned grid, int split, int subset, const int *subset_dev,
+                                 const float *x, const float *xT, float *g, float *gT, double *kl_part, int mode,
+                                 cudaStream_t st) {
+  const int win = P.tofw_win <= 4 ? 4 : (P.tofw_win <= 6 ? 6 : 8);
+  if (win == 4) return launch_tofk_w<K, 4>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
+  if (win == 6) return launch_tofk_w<K, 6>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
+  return launch_tofk_w<K, 8>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
+}
+
 cudaError_t launch_grad_tofk(const DevPlan &P, int K, int split, unsigned grid, int subset, const int *subset_dev,
                              const float *x, const float *xT, float *g, float *gT, double *kl_part, int mode,
                              cudaStream_t st) {
   note_launch();
-  const int win = P.tofw_win <= 4 ? 4 : (P.tofw_win <= 6 ? 6 : 8);
-  if (K == 2) {
-    if (win == 4) return launch_tofk_w<2, 4>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
-    if (win == 6) return launch_tofk_w<2, 6>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
-    return launch_tofk_w<2, 8>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
-  }
-  if (win == 4) return launch_tofk_w<1, 4>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
-  if (win == 6) return launch_tofk_w<1, 6>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
-  return launch_tofk_w<1, 8>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
+  if (K == 4) return launch_tofk_k<4>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
+  if (K == 2) return launch_tofk_k<2>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
+  return launch_tofk_k<1>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
 }
 
 }  // namespace petgb

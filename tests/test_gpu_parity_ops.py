@@ -356,7 +356,7 @@ def test_grad_launch_shapes(key, shape):
     c = case(key)
     k, parts = shape
     windowed = key in ("tof", "tof13", "tof5")
-    if c.plan.T > 1 and (k > (2 if windowed else 1) or parts > (8 if windowed else 4)):
+    if c.plan.T > 1 and (k > (4 if windowed else 1) or parts > (8 if windowed else 4)):
         pytest.skip("not a launch shape of this TOF kernel")
     c.plan.set_grad_shape(k, parts)
     try:
