@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-nrmse", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--mode", default="step", choices=["step", "grad", "configs", "study", "c4", "c5"],
+    ap.add_argument("--mode", default="step", choices=["step", "grad", "configs", "study", "c4", "c5", "update"],
                     help="grad: only the fused subset-gradient op, for profiler captures; "
                          "configs: SVRG outer-loop rates on the 2D, 3D and 3D TOF workloads; "
                          "study: epochs to 1%% NRMSE over algorithm x preconditioner x tau0 (2D)")
@@ -649,6 +649,29 @@ def run_c5(args, pet, dev):
                       "samples_per_s_fwd_and_back": 2 * samples / (kms / max(kn, 1) * 1e-3)}), flush=True)
 
 
+def run_update(args, pet, dev):
+    """SVRG outer loops on a workload (default c5p: the brain-scale image, whose SVRG table
+    of 25 subset gradients, 328 MB, exceeds L2) for captures of the estimator + step + prox
+    kernel; prints the loop time."""
+    import torch
+    cfg = args.config if args.config != "c2" else "c5p"
+    p, dt = load_workload(cfg, 0, dev)
+    n = p["nsub"]
+    plan = pet.Plan(p["geom"], n)
+    plan.set_data(dt["y"], dt["r"], dt["mu"], dt["sens"])
+    x = torch.from_numpy(np.maximum(p["x_true"], 0.05 * p["x_true"].max()).astype(np.float32)).to(dev)
+    solver = pet.Solver(plan, algo=pet.SVRG, beta=p["beta"], gamma=p["gamma"], eps=p["eps"], pc_iters=(0,), seed=9)
+    solver.set_image(x)
+    solver.run(2 * n * max(args.warmup, 1))
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    solver.run(2 * n * args.steps)
+    b.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "update", "config": cfg, "ms_per_outer_loop": a.elapsed_time(b) / args.steps}))
+
+
 def run_grad_only(args, pet, dev):
     """Subset gradients only (objective_grad on successive subsets), for ncu captures."""
     import torch
@@ -865,6 +888,8 @@ def main():
         return run_batched(args, pet, dev)
     if args.mode == "c5":
         return run_c5(args, pet, dev)
+    if args.mode == "update":
+        return run_update(args, pet, dev)
     import tempfile
     cfg = args.workload
     p, dt = load_workload(cfg, rank, dev)

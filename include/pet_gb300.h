@@ -286,14 +286,18 @@ long long pet_solver_subsets(const pet_solver *s, int *subsets, long long cap);
 
 /* Many independent reconstructions advanced together (batched instances of uneven image
  * and sinogram sizes, betas and count levels).  Each solver keeps its own plan, data,
- * options and subset order; the batch runs every iteration as one launch per phase
- * for all of them (fused subset gradient, RDP gradient, estimator + step + prox,
- * accumulator clear) and captures iters_per_graph iterations in one CUDA graph,
- * replayed after uploading each batch epoch's per-solver subsets and iteration indices.
- * Iteration windows that contain a preconditioner update, and a final partial window,
- * run per solver.  Requirements (else PET_ERR_UNSUPPORTED / PET_ERR_ARG): SGD or SAGA
- * (all the same), non-TOF plans, no kappa image, no deterministic mode, distinct plans
- * (a plan's scratch serves one solver at a time).  The solvers are borrowed. */
+ * options and subset order; the batch runs windows of iters_per_graph iterations, each
+ * iteration as one launch per phase for all instances (fused subset gradient, RDP
+ * gradient, estimator + step + prox, accumulator clear), captured once in a CUDA graph and
+ * replayed after uploading each window's per-solver subsets and iteration indices.  An
+ * instance whose window contains a preconditioner update or an SVRG snapshot refresh (n
+ * subset gradients and a step), and every instance in a final window shorter than
+ * iters_per_graph, runs that window alone (one iteration at a time, exactly as
+ * pet_solver_run); the batched launches then skip it.  Requirements (else
+ * PET_ERR_UNSUPPORTED / PET_ERR_ARG): SGD, SAGA or SVRG (all the same; SVRG with the
+ * table and without importance sampling), non-TOF plans, no kappa image, no
+ * deterministic mode, no resolution model, distinct plans (a plan's scratch serves one
+ * solver at a time).  The solvers are borrowed. */
 typedef struct pet_batch pet_batch;
 pet_status pet_batch_create(pet_solver *const *solvers, int n, int iters_per_graph, pet_batch **out);
 void pet_batch_destroy(pet_batch *b);

@@ -150,7 +150,8 @@ __global__ void __launch_bounds__(RDP_TX * RDP_TY) k_rdp(RdpArgs a, const float 
 // Batched RDP gradient (no kappa, gradient only): blocks [begin[j], begin[j+1]) belong
 // to job j.
 __global__ void __launch_bounds__(RDP_TX * RDP_TY) k_rdp_batch(const RdpJob *__restrict__ jobs,
-                                                                const int *__restrict__ begin, int njobs) {
+                                                                const int *__restrict__ begin, int njobs,
+                                                                const int *__restrict__ sub) {
   __shared__ int s_job;
   __shared__ RdpJob sj;
   const int tid = threadIdx.y * RDP_TX + threadIdx.x;
@@ -165,15 +166,16 @@ __global__ void __launch_bounds__(RDP_TX * RDP_TY) k_rdp_batch(const RdpJob *__r
     if (tid == 0) { s_job = job; sj = jobs[job]; }
   }
   __syncthreads();
+  if (sub && __ldg(&sub[s_job]) == kBatchSkip) return;  // whole block: one job
   rdp_body<false, true, false, false>(sj.a, sj.x, sj.grad, nullptr, nullptr, 0,
                                       (int)blockIdx.x - __ldg(&begin[s_job]));
 }
 
 cudaError_t launch_rdp_batch(const RdpJob *jobs, const int *begin, int njobs, int total_blocks,
-                             cudaStream_t st) {
+                             const int *sub, cudaStream_t st) {
   if (total_blocks <= 0) return cudaSuccess;
   note_launch();
-  k_rdp_batch<<<total_blocks, dim3(RDP_TX, RDP_TY), 0, st>>>(jobs, begin, njobs);
+  k_rdp_batch<<<total_blocks, dim3(RDP_TX, RDP_TY), 0, st>>>(jobs, begin, njobs, sub);
   return cudaGetLastError();
 }
 

@@ -64,6 +64,7 @@ static void plan_free(pet_plan *p) {
   cudaFree(p->d_tofw_tab);
   cudaFree(p->d_tof_grp2);
   cudaFree(p->d_tof_grp4);
+  cudaFree(p->d_tof_work);
   cudaFree(p->d_xs); cudaFree(p->d_rtmp);
   delete p;
 }
@@ -141,7 +142,7 @@ static pet_status build_tof_window(pet_plan *pl, const std::vector<float4> &plan
   };
   const std::vector<int> grp2 = groups(2), grp4 = groups(4);
   if (dalloc(&pl->d_tofw_tab, tab.size()) != cudaSuccess || dalloc(&pl->d_tof_grp2, grp2.size()) != cudaSuccess ||
-      dalloc(&pl->d_tof_grp4, grp4.size()) != cudaSuccess)
+      dalloc(&pl->d_tof_grp4, grp4.size()) != cudaSuccess || dalloc(&pl->d_tof_work, 1) != cudaSuccess)
     return PET_ERR_NOMEM;
   if (cudaMemcpy(pl->d_tofw_tab, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(pl->d_tof_grp2, grp2.data(), grp2.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -152,6 +153,11 @@ static pet_status build_tof_window(pet_plan *pl, const std::vector<float4> &plan
   dp.tof_ngrp2 = (int)(grp2.size() / 2);
   dp.tof_grp4 = pl->d_tof_grp4;
   dp.tof_ngrp4 = (int)(grp4.size() / 4);
+  dp.tof_work = pl->d_tof_work;
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, pl->device) != cudaSuccess || nsm < 1)
+    return PET_ERR_CUDA;
+  dp.nsm = nsm;
   return tofk_init_device() == cudaSuccess ? PET_OK : PET_ERR_CUDA;
 }
 

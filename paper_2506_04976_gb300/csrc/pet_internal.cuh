@@ -57,6 +57,8 @@ struct DevPlan {
   int tof_ngrp2;
   const int *tof_grp4;     // [tof_ngrp4][4] plane quadruples of equal axial slope (-1: none)
   int tof_ngrp4;
+  unsigned long long *tof_work;  // work counter of the persistent TOF kernel (plan scratch)
+  int nsm;                       // multiprocessors of the plan's device
 };
 
 // Windowed TOF kernel constants: threads per block, table rows per bin width (a power of
@@ -234,6 +236,10 @@ int max_split(const DevPlan &P);
 int max_planes(const DevPlan &P);
 cudaError_t launch_fill(float *p, size_t n, float v, cudaStream_t st);
 
+// Subset index that marks an instance of a batch as skipped for one batched iteration
+// (it runs that window alone).
+constexpr int kBatchSkip = -2;
+
 // One reconstruction of a batch, as seen by the batched fused-gradient kernel.
 struct GradJob {
   DevPlan P;
@@ -287,8 +293,9 @@ struct RdpJob {
   const float *x;
   float *grad;
 };
+// sub (may be NULL): per-job subsets of the iteration; jobs marked kBatchSkip are skipped.
 cudaError_t launch_rdp_batch(const RdpJob *jobs, const int *begin, int njobs, int total_blocks,
-                             cudaStream_t st);
+                             const int *sub, cudaStream_t st);
 cudaError_t launch_reduce_sum(const double *part, int n, double *out, int accumulate,
                               cudaStream_t st);
 cudaError_t launch_max(const float *x, size_t n, float *part, float *out, cudaStream_t st);

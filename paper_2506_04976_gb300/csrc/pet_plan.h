@@ -25,6 +25,7 @@ struct pet_plan {
   float4 *d_tofw_tab = nullptr; // TOF: rows of the interpolated bin-weight table (windowed kernel)
   int *d_tof_grp2 = nullptr;    // TOF: plane pairs of equal axial slope
   int *d_tof_grp4 = nullptr;    // TOF: plane quadruples of equal axial slope
+  unsigned long long *d_tof_work = nullptr;  // TOF: work counter of the persistent kernel
   // derived data
   float *d_m = nullptr;         // [V][P][R] multiplicative factors
   float *d_sens = nullptr;      // [N] A^T 1

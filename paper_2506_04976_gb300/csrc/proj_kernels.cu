@@ -491,6 +491,7 @@ __global__ void __launch_bounds__(kBlock) k_grad_mp_batch(const GradJob *__restr
   if (threadIdx.x == 0) sj = jobs[j];
   __syncthreads();
   const int subset = *sj.subset_dev;
+  if (subset == kBatchSkip) return;  // this instance runs the window alone (whole block)
   grad_mp_body<K, SPLIT>(sj.P, subset, (int)blockIdx.x - __ldg(&begin[j]), sj.x, sj.xT, sj.g, sj.gT, nullptr, mode);
 }
 

@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(256) k_update_batch(const UpdArgs *__restrict_
   const int j = batch_job(begin, njobs);
   if (threadIdx.x == 0 && threadIdx.y == 0) sa = jobs[j];
   __syncthreads();
+  if (*sa.subset_dev == kBatchSkip) return;  // this instance runs the window alone (whole block)
   const int blk = (int)blockIdx.x - __ldg(&begin[j]);
   const int tx = (sa.nx + 31) / 32, ty = (sa.ny + 31) / 32;
   upd_body<ALGO>(sa, blk % tx, (blk / tx) % ty, blk / (tx * ty));
@@ -194,8 +195,9 @@ struct ClearJob {
 };
 
 __global__ void __launch_bounds__(256) k_clear_batch(const ClearJob *__restrict__ jobs, const int *__restrict__ begin,
-                                                     int njobs) {
+                                                     int njobs, const int *__restrict__ sub) {
   const int j = batch_job(begin, njobs);
+  if (sub && __ldg(&sub[j]) == kBatchSkip) return;  // whole block: one job
   const ClearJob c = jobs[j];
   const int b0 = __ldg(&begin[j]), nb = __ldg(&begin[j + 1]) - b0;
   const size_t n4 = c.N / 4;
@@ -1002,6 +1004,7 @@ struct pet_batch {
   cudaStream_t cap = nullptr;
   cudaStream_t side = nullptr;  // the prior's gradients, concurrent with the subset gradients
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  std::vector<char> after_single;  // instance ran its last iteration alone (accumulators to clear)
 };
 
 static void batch_free(pet_batch *b) {
@@ -1030,7 +1033,9 @@ extern "C" pet_status pet_batch_create(pet_solver *const *solvers, int n, int it
   for (int i = 0; i < n; ++i) {
     const pet_solver *si = solvers[i];
     if (!si) return PET_ERR_ARG;
-    if (si->o.algo != solvers[0]->o.algo || si->o.algo == PET_SVRG || si->o.deterministic) return PET_ERR_UNSUPPORTED;
+    if (si->o.algo != solvers[0]->o.algo || si->o.deterministic || si->o.low_memory ||
+        si->o.sampling == PET_SAMPLE_IMPORTANCE)
+      return PET_ERR_UNSUPPORTED;
     if (si->plan->T != 1 || si->o.kappa) return PET_ERR_UNSUPPORTED;
     for (int j = 0; j < i; ++j)
       if (solvers[j]->plan == si->plan || solvers[j] == si) return PET_ERR_ARG;  // scratch is per plan
@@ -1038,6 +1043,7 @@ extern "C" pet_status pet_batch_create(pet_solver *const *solvers, int n, int it
   }
   pet_batch *b = new pet_batch();
   b->s.assign(solvers, solvers + n);
+  b->after_single.assign(n, 1);  // the solvers may have run alone before
   b->nj = n;
   b->E = iters_per_graph;
   b->algo = solvers[0]->o.algo;
@@ -1125,17 +1131,18 @@ static pet_status batch_iteration(pet_batch *b, int j, cudaStream_t st) {
   const int n = b->nj;
   SCK(cudaEventRecord(b->ev_fork, st));
   SCK(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
-  SCK(launch_rdp_batch(b->d_rjobs, b->d_rbegin, n, b->rblocks, b->side));
+  const int *sub = b->d_sub + (size_t)j * n;
+  SCK(launch_rdp_batch(b->d_rjobs, b->d_rbegin, n, b->rblocks, sub, b->side));
   SCK(cudaEventRecord(b->ev_join, b->side));
   SCK(launch_grad_batch(b->d_gjobs + (size_t)j * n, b->d_gbegin, n, b->gblocks, b->K, b->split, st));
   SCK(cudaStreamWaitEvent(st, b->ev_join, 0));
   note_launch();
-  if (b->algo == PET_SAGA)
-    k_update_batch<1><<<b->ublocks, dim3(32, 8), 0, st>>>(b->d_ujobs + (size_t)j * n, b->d_ubegin, n);
-  else
-    k_update_batch<0><<<b->ublocks, dim3(32, 8), 0, st>>>(b->d_ujobs + (size_t)j * n, b->d_ubegin, n);
+  const UpdArgs *uj = b->d_ujobs + (size_t)j * n;
+  if (b->algo == PET_SAGA) k_update_batch<1><<<b->ublocks, dim3(32, 8), 0, st>>>(uj, b->d_ubegin, n);
+  else if (b->algo == PET_SVRG) k_update_batch<2><<<b->ublocks, dim3(32, 8), 0, st>>>(uj, b->d_ubegin, n);
+  else k_update_batch<0><<<b->ublocks, dim3(32, 8), 0, st>>>(uj, b->d_ubegin, n);
   note_launch();
-  k_clear_batch<<<b->cblocks, 256, 0, st>>>(b->d_cjobs, b->d_cbegin, n);
+  k_clear_batch<<<b->cblocks, 256, 0, st>>>(b->d_cjobs, b->d_cbegin, n, sub);
   SCK(cudaGetLastError());
   return PET_OK;
 }
@@ -1215,12 +1222,22 @@ extern "C" pet_status pet_batch_autotune(pet_batch *b, void *stream, int *planes
   e = batch_tables(b);
   if (e != PET_OK) return e;
   note_launch();
-  k_clear_batch<<<b->cblocks, 256, 0, st>>>(b->d_cjobs, b->d_cbegin, b->nj);  // discard the trial gradients
+  k_clear_batch<<<b->cblocks, 256, 0, st>>>(b->d_cjobs, b->d_cbegin, b->nj, nullptr);  // discard the trial gradients
   SCK(cudaGetLastError());
   SCK(cudaStreamSynchronize(st));
   if (planes_per_thread) *planes_per_thread = bk;
   if (parts) *parts = bs;
   return PET_OK;
+}
+
+// An iteration in [k0, k0 + len) that the batched phases cannot run for this solver: a
+// preconditioner update or an SVRG snapshot refresh (n subset gradients and a step).
+static bool window_has_event(const pet_solver *s, long long k0, long long len) {
+  if (epoch_has_pc(s, k0, len)) return true;
+  if (s->o.algo != PET_SVRG) return false;
+  const long long period = (long long)s->o.omega * s->n;
+  const long long next = ((k0 + period - 1) / period) * period;  // first refresh at or after k0
+  return next < k0 + len;
 }
 
 extern "C" pet_status pet_batch_run(pet_batch *b, long long niter, void *stream) {
@@ -1233,34 +1250,43 @@ extern "C" pet_status pet_batch_run(pet_batch *b, long long niter, void *stream)
   if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
   const int n = b->nj, E = b->E;
   long long done = 0;
-  bool after_single = true;  // the solvers may have run alone before this call
+  std::vector<char> alone(n);
   while (done < niter) {
-    bool plain = niter - done < E;
-    for (pet_solver *s : b->s)
-      if (epoch_has_pc(s, s->k, E)) plain = true;
-    if (plain) {
-      for (pet_solver *s : b->s) {
+    // An instance whose window holds an event (or a final window shorter than E) runs the
+    // window alone, iteration by iteration; the others run the captured batched window,
+    // in which the lone instances are marked kBatchSkip.
+    const long long len = std::min<long long>(E, niter - done);
+    int nalone = 0;
+    for (int i = 0; i < n; ++i) {
+      alone[i] = len < E || window_has_event(b->s[i], b->s[i]->k, E);
+      nalone += alone[i];
+    }
+    for (int i = 0; i < n; ++i) {
+      if (!alone[i]) continue;
+      pet_solver *s = b->s[i];
+      for (long long j = 0; j < len; ++j) {
         e = iterate(s, s->k, subset_of(s, s->k), st);
         if (e != PET_OK) return e;
         s->k += 1;
       }
-      after_single = true;
-      done += 1;
-      continue;
+      b->after_single[i] = 1;
     }
+    done += len;
+    if (nalone == n) continue;
     // A single-solver iteration leaves its accumulator pair for the next one to clear;
     // the batched phases use (g, the plan's transposed accumulator), so clear it here
     // (after single-solver iterations only: a batched window leaves both clean).
-    if (after_single) {
-      for (pet_solver *s : b->s) {
-        if (s->k <= 0) continue;
+    for (int i = 0; i < n; ++i) {
+      pet_solver *s = b->s[i];
+      if (alone[i] || !b->after_single[i]) continue;
+      if (s->k > 0) {
         const int pb = (int)((s->k - 1) & 1);
         note_launch();
         k_clear2<<<grid_elems(s->N / 4), 256, 0, st>>>(s->gbuf[pb], s->gTbuf[pb], s->N);
       }
-      SCK(cudaGetLastError());
-      after_single = false;
+      b->after_single[i] = 0;
     }
+    SCK(cudaGetLastError());
     if (!b->exec) {
       cudaGraph_t graph = nullptr;
       const long long before = launch_count();
@@ -1281,7 +1307,7 @@ extern "C" pet_status pet_batch_run(pet_batch *b, long long niter, void *stream)
     for (int j = 0; j < E; ++j)
       for (int i = 0; i < n; ++i) {
         pet_solver *s = b->s[i];
-        b->h_sub[bb][(size_t)j * n + i] = subset_of(s, s->k + j);
+        b->h_sub[bb][(size_t)j * n + i] = alone[i] ? kBatchSkip : subset_of(s, s->k + j);
         b->h_k[bb][(size_t)j * n + i] = s->k + j;
       }
     SCK(cudaMemcpyAsync(b->d_sub, b->h_sub[bb], (size_t)E * n * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -1289,8 +1315,8 @@ extern "C" pet_status pet_batch_run(pet_batch *b, long long niter, void *stream)
     SCK(cudaEventRecord(b->up[bb], st));
     SCK(cudaGraphLaunch(b->exec, st));
     note_launch(4LL * E);
-    for (pet_solver *s : b->s) s->k += E;
-    done += E;
+    for (int i = 0; i < n; ++i)
+      if (!alone[i]) b->s[i]->k += E;
   }
   return PET_OK;
 }

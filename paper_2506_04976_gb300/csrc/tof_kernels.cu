@@ -28,6 +28,7 @@
 // keeps its own window; the bin sums are combined in a fixed order with compensation.
 // With one part a thread owns its LORs from the forward sums to the backprojection, so
 // no block barrier separates the phases.
+#include <algorithm>
 #include <climits>
 
 #include "pet_internal.cuh"
@@ -105,39 +106,19 @@ __device__ __forceinline__ void win_weights(const float4 *__restrict__ tab, int 
 
 }  // namespace
 
-// Fused TOF gradient: forward (windowed TOF sums), KL ratio, backprojection.  NT threads
-// per block; dynamic shared memory: the weight table (kTofM rows of WIN/2 float4) then the
-// bin sums / ratios s_acc[(k T + b) NT + tid].
+// One LOR group (K planes of one view and radial bin; part `part` of SPLIT) from the forward
+// TOF sums to the backprojection; returns this thread's share of the KL value.  s_acc is
+// the block's bin array (column tid of each row belongs to this thread; with SPLIT > 1 the
+// parts of LOR group tl exchange sums through columns j LPB + tl, so every thread of the
+// block must call this together).  The caller has cleared this thread's column.
 template <int K, int WIN, int SPLIT, int NT>
-__global__ void __launch_bounds__(NT, 2) k_grad_tofk(DevPlan P, int subset, const int *subset_dev,
-                                                             const float *__restrict__ x, const float *__restrict__ xT,
-                                                             float *__restrict__ g, float *__restrict__ gT,
-                                                             double *__restrict__ kl_part, int mode) {
-  constexpr int LPB = NT / SPLIT;  // LOR groups per block
+__device__ __forceinline__ double tof_group(const DevPlan &P, const float4 *__restrict__ s_tab, float *s_acc,
+                                            int v, int r, int grp, bool ok, int part, int tl, int tid,
+                                            const float *__restrict__ x, const float *__restrict__ xT,
+                                            float *__restrict__ g, float *__restrict__ gT, int mode, bool want_kl) {
+  constexpr int LPB = NT / SPLIT;
   constexpr int WP = WIN / 2;
-  extern __shared__ float4 s_dyn[];
-  float4 *s_tab = s_dyn;
-  float *s_acc = reinterpret_cast<float *>(s_dyn + kTofM * WP);
-  const int tid = threadIdx.x;
-  for (int k = tid; k < kTofM * WP; k += NT) s_tab[k] = __ldg(&P.tofw_tab[k]);
   const int T = P.T;
-  for (int k = 0; k < K * T; ++k) s_acc[k * NT + tid] = 0.f;
-  if (subset_dev) subset = *subset_dev;
-  const int part = tid / LPB;
-  const int tl = tid % LPB;
-  const int nsub = subset < 0 ? 1 : P.nsub;
-  const int s0 = subset < 0 ? 0 : subset;
-  const int nv = (P.nview - s0 + nsub - 1) / nsub;
-  const int ngrp = K == 1 ? P.nplane : (K == 2 ? P.tof_ngrp2 : P.tof_ngrp4);
-  const long long uid = (long long)blockIdx.x * LPB + tl;
-  const bool ok = uid < (long long)nv * ngrp * P.nrad;
-  int v = 0, r = 0, grp = 0;
-  if (ok) {
-    r = (int)(uid % P.nrad);
-    const long long t = uid / P.nrad;
-    grp = (int)(t % ngrp);
-    v = s0 + (int)(t / ngrp) * nsub;
-  }
   // shared in-plane geometry and the planes of the group
   const float4 vw = __ldg(&P.view[v]);
   const float4 vr = __ldg(&P.vr[v * P.nrad + r]);
@@ -188,8 +169,6 @@ __global__ void __launch_bounds__(NT, 2) k_grad_tofk(DevPlan P, int subset, cons
   const float xs0 = fmaf(sg * t0b * sec, P.tofw_inv_h, P.tofw_off);
   const float dxs = sg * dau * sec * P.tofw_inv_h;
   const int umax = (T + WIN + 4) * kTofM;
-  __syncthreads();  // table and cleared sums ready
-
   if (mode != MODE_SENS) {
     float2 acc[K][WP];  // bins (2p, 2p+1) of the window for each plane
 #pragma unroll
@@ -287,10 +266,10 @@ __global__ void __launch_bounds__(NT, 2) k_grad_tofk(DevPlan P, int subset, cons
         if (!(ybar > 0.f)) {
           if (yb > 0.f) atomicOr(P.err, 1);
           q = (grad_like(mode) && yb == 0.f) ? mL : 0.f;
-          if (kl_part && yb == 0.f) kl += (double)fmaxf(ybar, 0.f);
+          if (want_kl && yb == 0.f) kl += (double)fmaxf(ybar, 0.f);
         } else {
           q = grad_like(mode) ? mL * (1.f - yb / ybar) : (mode == MODE_EM ? mL * (yb / ybar) : 0.f);
-          if (kl_part) {
+          if (want_kl) {
             const double db = ybar, dy = yb;
             kl += (yb > 0.f) ? (db - dy + dy * log(dy / db)) : db;
           }
@@ -367,8 +346,92 @@ __global__ void __launch_bounds__(NT, 2) k_grad_tofk(DevPlan P, int subset, cons
       }
     }
   }
+  return kl;
+}
+
+// Fused TOF gradient: forward (windowed TOF sums), KL ratio, backprojection.  NT threads
+// per block, one LOR group per thread (or part); dynamic shared memory: the weight table
+// (kTofM rows of WIN/2 float4) then the bin sums / ratios s_acc[(k T + b) NT + tid].
+template <int K, int WIN, int SPLIT, int NT>
+__global__ void __launch_bounds__(NT, 2) k_grad_tofk(DevPlan P, int subset, const int *subset_dev,
+                                                     const float *__restrict__ x, const float *__restrict__ xT,
+                                                     float *__restrict__ g, float *__restrict__ gT,
+                                                     double *__restrict__ kl_part, int mode) {
+  constexpr int LPB = NT / SPLIT;  // LOR groups per block
+  extern __shared__ float4 s_dyn[];
+  float4 *s_tab = s_dyn;
+  float *s_acc = reinterpret_cast<float *>(s_dyn + kTofM * (WIN / 2));
+  const int tid = threadIdx.x;
+  for (int k = tid; k < kTofM * (WIN / 2); k += NT) s_tab[k] = __ldg(&P.tofw_tab[k]);
+  for (int k = 0; k < K * P.T; ++k) s_acc[k * NT + tid] = 0.f;
+  if (subset_dev) subset = *subset_dev;
+  const int part = tid / LPB;
+  const int tl = tid % LPB;
+  const int nsub = subset < 0 ? 1 : P.nsub;
+  const int s0 = subset < 0 ? 0 : subset;
+  const int nv = (P.nview - s0 + nsub - 1) / nsub;
+  const int ngrp = K == 1 ? P.nplane : (K == 2 ? P.tof_ngrp2 : P.tof_ngrp4);
+  const long long uid = (long long)blockIdx.x * LPB + tl;
+  const bool ok = uid < (long long)nv * ngrp * P.nrad;
+  int v = 0, r = 0, grp = 0;
+  if (ok) {
+    r = (int)(uid % P.nrad);
+    const long long t = uid / P.nrad;
+    grp = (int)(t % ngrp);
+    v = s0 + (int)(t / ngrp) * nsub;
+  }
+  __syncthreads();  // table and cleared sums ready
+  const double kl = tof_group<K, WIN, SPLIT, NT>(P, s_tab, s_acc, v, r, grp, ok, part, tl, tid, x, xT, g, gT, mode,
+                                                 kl_part != nullptr);
   if (kl_part) {
     const double s = block_sum<NT>(kl);
+    if (tid == 0) kl_part[blockIdx.x] = s;
+  }
+}
+
+// Persistent form with one part per LOR: a few blocks per SM load the table once, and each
+// warp takes work units (32 consecutive radial bins of one view and plane group) from a
+// counter in device memory (cleared before the launch) until none is left, so that no SM
+// idles while a block waits for its slowest warp.
+template <int K, int WIN, int NT>
+__global__ void __launch_bounds__(NT, 2) k_grad_tofp(DevPlan P, int subset, const int *subset_dev,
+                                                     const float *__restrict__ x, const float *__restrict__ xT,
+                                                     float *__restrict__ g, float *__restrict__ gT,
+                                                     double *__restrict__ kl_part, int mode) {
+  extern __shared__ float4 s_dyn[];
+  float4 *s_tab = s_dyn;
+  float *s_acc = reinterpret_cast<float *>(s_dyn + kTofM * (WIN / 2));
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int k = tid; k < kTofM * (WIN / 2); k += NT) s_tab[k] = __ldg(&P.tofw_tab[k]);
+  if (subset_dev) subset = *subset_dev;
+  const int nsub = subset < 0 ? 1 : P.nsub;
+  const int s0 = subset < 0 ? 0 : subset;
+  const int nv = (P.nview - s0 + nsub - 1) / nsub;
+  const int ngrp = K == 1 ? P.nplane : (K == 2 ? P.tof_ngrp2 : P.tof_ngrp4);
+  const int nchunk = (P.nrad + 31) / 32;
+  const long long units = (long long)nv * ngrp * nchunk;
+  // per-thread KL sums live in shared memory, not in registers across the unit loop
+  __shared__ double s_kl[NT];
+  s_kl[tid] = 0.0;
+  __syncthreads();  // table ready
+  for (;;) {
+    long long u = 0;
+    if (lane == 0) u = atomicAdd(reinterpret_cast<unsigned long long *>(P.tof_work), 1ULL);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= units) break;  // warp-uniform
+    const int chunk = (int)(u % nchunk);
+    const long long t = u / nchunk;
+    const int grp = (int)(t % ngrp);
+    const int v = s0 + (int)(t / ngrp) * nsub;
+    const int r = chunk * 32 + lane;
+    const bool ok = r < P.nrad;
+    for (int k = 0; k < K * P.T; ++k) s_acc[k * NT + tid] = 0.f;
+    const double kl = tof_group<K, WIN, 1, NT>(P, s_tab, s_acc, v, ok ? r : 0, grp, ok, 0, tid, tid, x, xT, g, gT,
+                                               mode, kl_part != nullptr);
+    if (kl_part) s_kl[tid] += kl;
+  }
+  if (kl_part) {
+    const double s = block_sum<NT>(s_kl[tid]);
     if (tid == 0) kl_part[blockIdx.x] = s;
   }
 }
@@ -385,8 +448,14 @@ bool tofk_supported(const DevPlan &P, int K) {
 
 int tofk_blocks(const DevPlan &P, int nv, int K, int split) {
   const long long ngrp = K == 1 ? P.nplane : (K == 2 ? P.tof_ngrp2 : P.tof_ngrp4);
+  const int nt = K == 4 ? tofk_nt<4>() : kTofBlock;
+  if (split == 1) {  // persistent: two blocks per SM, or fewer when there is less work
+    const long long units = (long long)nv * ngrp * ((P.nrad + 31) / 32);
+    const long long need = (units + nt / 32 - 1) / (nt / 32);
+    return (int)std::min<long long>(need, 2LL * P.nsm);
+  }
   const long long units = (long long)nv * ngrp * P.nrad;
-  const int lpb = (K == 4 ? tofk_nt<4>() : kTofBlock) / split;
+  const int lpb = nt / split;
   return (int)((units + lpb - 1) / lpb);
 }
 
@@ -395,7 +464,13 @@ static cudaError_t launch_tofk_t(const DevPlan &P, unsigned grid, int subset, co
                                  const float *xT, float *g, float *gT, double *kl_part, int mode, cudaStream_t st) {
   constexpr int NT = tofk_nt<K>();
   const size_t smem = (size_t)kTofM * (WIN / 2) * sizeof(float4) + (size_t)K * P.T * NT * sizeof(float);
-  k_grad_tofk<K, WIN, SPLIT, NT><<<grid, NT, smem, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
+  if (SPLIT == 1) {
+    cudaError_t e = cudaMemsetAsync(P.tof_work, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    k_grad_tofp<K, WIN, NT><<<grid, NT, smem, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
+  } else {
+    k_grad_tofk<K, WIN, SPLIT, NT><<<grid, NT, smem, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
+  }
   return cudaGetLastError();
 }
 
@@ -404,8 +479,9 @@ static cudaError_t launch_tofk_t(const DevPlan &P, unsigned grid, int subset, co
 template <int K, int WIN, int SPLIT>
 static cudaError_t tofk_attr() {
   constexpr int NT = tofk_nt<K>();
-  return cudaFuncSetAttribute(k_grad_tofk<K, WIN, SPLIT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(kTofM * (WIN / 2) * sizeof(float4) + K * kTofMaxBins * NT * sizeof(float)));
+  const int bytes = (int)(kTofM * (WIN / 2) * sizeof(float4) + K * kTofMaxBins * NT * sizeof(float));
+  if (SPLIT == 1) return cudaFuncSetAttribute(k_grad_tofp<K, WIN, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return cudaFuncSetAttribute(k_grad_tofk<K, WIN, SPLIT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 template <int K, int WIN>

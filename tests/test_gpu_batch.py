@@ -1,6 +1,8 @@
 """Batched instances (uneven sizes, betas, count levels and subset counts) advanced by
 one launch per phase: each instance's result equals the same solver run alone (up to
-the atomics' summation order) and, for one instance, the FP64 oracle's trajectory."""
+the atomics' summation order) and, for one instance, the FP64 oracle's trajectory.  With
+SVRG every snapshot refresh (and every preconditioner update) makes its instance run
+that window alone while the others stay batched."""
 import numpy as np
 import pytest
 
@@ -35,21 +37,25 @@ def _instances():
     return out
 
 
-def _solver(pet, p, plan, x0, seed, algo):
+def _solver(pet, p, plan, x0, seed, algo, step_rule=None):
     n = p["nsub"]
-    s = pet.Solver(plan, algo=algo, step_rule=pet.STEP_VANISH, tau0=1.0, eta=0.02, precond_kind=1,
-                   pc_iters=(0, n), beta=p["beta"], gamma=p["gamma"], eps=p["eps"], seed=seed)
+    s = pet.Solver(plan, algo=algo, step_rule=pet.STEP_VANISH if step_rule is None else step_rule, tau0=1.0,
+                   eta=0.02, precond_kind=1, pc_iters=(0, n), beta=p["beta"], gamma=p["gamma"], eps=p["eps"],
+                   seed=seed)
     s.set_image(torch.from_numpy(x0).to(DEV))
     return s
 
 
-@pytest.mark.parametrize("algo", ["saga", "sgd"])
+@pytest.mark.parametrize("algo", ["saga", "sgd", "svrg", "svrg_bb"])
 def test_batch_matches_single_runs_and_oracle(algo):
     from paper_2506_04976_gb300 import binding as pet
-    A = pet.SAGA if algo == "saga" else pet.SGD
+    A = {"saga": pet.SAGA, "sgd": pet.SGD}.get(algo, pet.SVRG)
+    rule = pet.STEP_BB if algo == "svrg_bb" else pet.STEP_VANISH
     inst = _instances()
     E, niter = 4, 3 * 4 + 19  # graph epochs, plain windows (preconditioner updates) and a tail
-    solvers = [_solver(pet, p, plan, x0, 100 + i, A) for i, (p, plan, _, _, x0) in enumerate(inst)]
+    if A == pet.SVRG:
+        niter = 2 * 16 + 11  # several snapshot refreshes of every instance
+    solvers = [_solver(pet, p, plan, x0, 100 + i, A, rule) for i, (p, plan, _, _, x0) in enumerate(inst)]
     b = pet.Batch(solvers, iters_per_graph=E)
     b.run(niter)
     torch.cuda.synchronize()
@@ -57,19 +63,22 @@ def test_batch_matches_single_runs_and_oracle(algo):
     taus_b = [s.taus() for s in solvers]
     del b
     for i, (p, plan, mu32, sens32, x0) in enumerate(inst):
-        s1 = _solver(pet, p, plan, x0, 100 + i, A)
+        s1 = _solver(pet, p, plan, x0, 100 + i, A, rule)
         s1.run(niter)
         torch.cuda.synchronize()
         x1 = s1.image().cpu().numpy().astype(np.float64)
         assert np.linalg.norm(xb[i] - x1) <= 1e-5 * np.linalg.norm(x1), i
-        assert np.array_equal(taus_b[i], s1.taus())
+        if rule == pet.STEP_BB:  # BB steps: ratios of FP64 dot products of FP32 images
+            assert np.allclose(taus_b[i], s1.taus(), rtol=1e-5)
+        else:
+            assert np.array_equal(taus_b[i], s1.taus())
     # instance 1 (3D) against the oracle with the same subset order
     p, plan, mu32, sens32, x0 = inst[1]
     G = O.Geometry(p["geom"])
     m = O.multiplicative(G, mu32, sens32)
     n = p["nsub"]
     xo, _, _ = O.solve(G, x0, m, p["r"], p["y"], O.sensitivity(G, 1, -1, m), algo=A, nsub=n, niter=niter,
-                       order=O.subset_order(101, n, niter), step_rule=O.STEP_VANISH, tau0=1.0, eta=0.02,
+                       order=O.subset_order(101, n, niter), step_rule=rule, tau0=1.0, eta=0.02,
                        precond_kind=1, pc_iters=(0, n), beta=p["beta"], gamma=p["gamma"], eps=p["eps"])
     assert np.linalg.norm(xb[1] - xo) <= 1e-4 * np.linalg.norm(xo)
 
@@ -95,16 +104,19 @@ def test_batch_autotune_and_shapes():
             assert np.linalg.norm(a - c) <= 1e-5 * np.linalg.norm(a)
 
 
-def test_batch_rejects_shared_plans_and_svrg():
+def test_batch_rejects_shared_plans_and_unsupported_options():
     from paper_2506_04976_gb300 import binding as pet
     p, plan, _, _, x0 = _instances()[0]
     s1 = _solver(pet, p, plan, x0, 1, pet.SAGA)
     s2 = _solver(pet, p, plan, x0, 2, pet.SAGA)
     with pytest.raises(pet.PetError):
         pet.Batch([s1, s2])
-    s3 = pet.Solver(plan, algo=pet.SVRG, beta=p["beta"])
+    s3 = pet.Solver(plan, algo=pet.SVRG, beta=p["beta"], sampling=pet.SAMPLE_IMPORTANCE)
     with pytest.raises(pet.PetError):
         pet.Batch([s3])
+    s4 = pet.Solver(plan, algo=pet.SVRG, beta=p["beta"], low_memory=True)
+    with pytest.raises(pet.PetError):
+        pet.Batch([s4])
 
 
 def test_c4_specs_shape():
