@@ -199,6 +199,8 @@ def load_workload(cfg, seed, dev):
         p = synth.make_problem_device(cfg, seed, device=dev) if cfg != "c5p" else \
             synth.make_problem_device("c5", seed, device=dev, nview=50)
         dt = dict(y=p["y"], r=p["r"], sens=p["sens"], mu=torch.from_numpy(p["mu"].astype(np.float32)).to(dev))
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()  # return the generator's temporaries to the device
     else:
         p = synth.make_problem(cfg, seed)
         y = p["y"].view(np.int16) if p["y"].dtype == np.uint16 else p["y"].astype(np.int32)
