@@ -152,10 +152,115 @@ __device__ __forceinline__ void upd_body(const UpdArgs &a, int bx, int by, int z
   }
 }
 
+// The same update for images larger than the L2 share of the step (every operand comes
+// from HBM): a thread first issues the loads of all four of its rows (and of the
+// transposed gradient part), then computes and stores, so that more bytes are in flight
+// per thread.  Results are identical to upd_body.
+template <int ALGO>
+__device__ __forceinline__ void upd_body_ilp(const UpdArgs &a, int bx, int by, int z) {
+  __shared__ float tin[32][33];
+  __shared__ float tout[32][33];
+  __shared__ float s_tau, s_w;
+  __shared__ int s_sub;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x0 = bx * 32, y0 = by * 32;
+  const size_t sl = (size_t)z * a.nx * a.ny;
+  if (tx == 0 && ty == 0) {
+    const long long k = a.k_dev ? *a.k_dev : a.k;
+    s_tau = step_of(a, k);
+    s_sub = a.subset_dev ? *a.subset_dev : a.subset;
+    s_w = a.w_dev ? *a.w_dev : (float)a.n;
+    if (bx == 0 && by == 0 && z == 0) {
+      if (a.tau_log) a.tau_log[k] = s_tau;
+      if (a.sub_log) a.sub_log[k] = ALGO == 3 ? -1 : s_sub;
+    }
+  }
+  // the subset (table entry) is known to thread 0 only before the barrier; every other
+  // operand is loaded now
+  constexpr int R = 4;  // rows per thread
+  bool in[R];
+  size_t idx[R];
+  float gv[R], sv[R], Dv[R], xv[R], Gv[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int xx = x0 + tx, yy = y0 + ty + 8 * q;
+    in[q] = xx < a.nx && yy < a.ny;
+    idx[q] = in[q] ? sl + (size_t)yy * a.nx + xx : 0;
+    gv[q] = (ALGO != 3 && in[q]) ? a.g[idx[q]] : 0.f;
+    sv[q] = in[q] ? a.gS[idx[q]] : 0.f;
+    Dv[q] = in[q] ? a.D[idx[q]] : 0.f;
+    xv[q] = in[q] ? a.x[idx[q]] : 0.f;
+    Gv[q] = (ALGO != 0 && in[q]) ? a.G[idx[q]] : 0.f;
+  }
+  if (ALGO != 3) {
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int j = ty + 8 * q;
+      const int xx = x0 + j, yy = y0 + tx;
+      float v = 0.f;
+      if (xx < a.nx && yy < a.ny) v = a.gT[sl + (size_t)xx * a.ny + yy];
+      tin[j][tx] = v;
+    }
+  }
+  __syncthreads();
+  const float tau = s_tau;
+  const float nf = (float)a.n;
+  float *Ti = a.table ? a.table + (size_t)s_sub * a.N : nullptr;
+  float tv[R], hv[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    tv[q] = ((ALGO == 1 || ALGO == 2) && Ti && in[q]) ? Ti[idx[q]] : 0.f;
+    hv[q] = (ALGO == 2 && a.gSh && in[q]) ? a.gSh[idx[q]] : 0.f;
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int j = ty + 8 * q;
+    float xn = 0.f;
+    if (in[q]) {
+      float dir;
+      if (ALGO == 3) {
+        dir = Gv[q] + sv[q];
+      } else {
+        const float gi = gv[q] + tin[tx][j];
+        if (ALGO == 0) {
+          dir = fmaf(nf, gi, sv[q]);
+        } else if (ALGO == 1) {
+          const float gf = fmaf(sv[q], 1.f / nf, gi);
+          dir = fmaf(nf, gf - tv[q], Gv[q]);
+          a.G[idx[q]] = Gv[q] + (gf - tv[q]);
+          Ti[idx[q]] = gf;
+        } else {
+          const float w = s_w;
+          dir = fmaf(w, Ti ? gi - tv[q] : gi, Gv[q]) + sv[q];
+          if (a.gSh) dir = fmaf(w / nf - 1.f, sv[q] - hv[q], dir);
+        }
+      }
+      xn = fmaf(-tau * Dv[q], dir, xv[q]);
+      xn = xn > 0.f ? xn : 0.f;
+      a.x[idx[q]] = xn;
+    }
+    tout[tx][j] = xn;
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int xx = x0 + j, yy = y0 + tx;
+    if (xx < a.nx && yy < a.ny) a.xT[sl + (size_t)xx * a.ny + yy] = tout[j][tx];
+  }
+}
+
 template <int ALGO>
 __global__ void __launch_bounds__(256) k_update(UpdArgs a) {
   upd_body<ALGO>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
+
+template <int ALGO>
+__global__ void __launch_bounds__(256) k_update_ilp(UpdArgs a) {
+  upd_body_ilp<ALGO>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Images whose update operands (six or seven image-sized arrays) exceed about half of the
+// L2 cache take the variant with all loads issued first.
+constexpr size_t kUpdIlpVoxels = (size_t)2 << 20;
 
 // Job of this block among consecutive block ranges [begin[j], begin[j+1]).
 __device__ __forceinline__ int batch_job(const int *__restrict__ begin, int njobs) {
@@ -840,7 +945,8 @@ static pet_status iterate(pet_solver *s, long long k, int sub, cudaStream_t st) 
     note_launch();
     k_bb_final<<<1, 256, 0, st>>>(s->part, (int)ge, s->st, s->o.bb_until <= 0 || k <= s->o.bb_until ? 1 : 0);
     note_launch();
-    k_update<3><<<tile_grid(s), dim3(32, 8), 0, st>>>(upd_args(s, -1, k));
+    if (s->N >= kUpdIlpVoxels) k_update_ilp<3><<<tile_grid(s), dim3(32, 8), 0, st>>>(upd_args(s, -1, k));
+    else k_update<3><<<tile_grid(s), dim3(32, 8), 0, st>>>(upd_args(s, -1, k));
   } else {
     const int *sub_dev = nullptr;
     if (importance) {
@@ -864,9 +970,17 @@ static pet_status iterate(pet_solver *s, long long k, int sub, cudaStream_t st) 
     a.g = gk;
     a.gT = gTk;
     note_launch();
-    if (s->o.algo == PET_SGD) k_update<0><<<tile_grid(s), dim3(32, 8), 0, st>>>(a);
-    else if (s->o.algo == PET_SAGA) k_update<1><<<tile_grid(s), dim3(32, 8), 0, st>>>(a);
-    else k_update<2><<<tile_grid(s), dim3(32, 8), 0, st>>>(a);
+    const bool ilp = s->N >= kUpdIlpVoxels;
+    if (s->o.algo == PET_SGD) {
+      if (ilp) k_update_ilp<0><<<tile_grid(s), dim3(32, 8), 0, st>>>(a);
+      else k_update<0><<<tile_grid(s), dim3(32, 8), 0, st>>>(a);
+    } else if (s->o.algo == PET_SAGA) {
+      if (ilp) k_update_ilp<1><<<tile_grid(s), dim3(32, 8), 0, st>>>(a);
+      else k_update<1><<<tile_grid(s), dim3(32, 8), 0, st>>>(a);
+    } else {
+      if (ilp) k_update_ilp<2><<<tile_grid(s), dim3(32, 8), 0, st>>>(a);
+      else k_update<2><<<tile_grid(s), dim3(32, 8), 0, st>>>(a);
+    }
   }
   SCK(cudaGetLastError());
   return PET_OK;

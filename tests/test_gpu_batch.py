@@ -53,8 +53,13 @@ def test_batch_matches_single_runs_and_oracle(algo):
     rule = pet.STEP_BB if algo == "svrg_bb" else pet.STEP_VANISH
     inst = _instances()
     E, niter = 4, 3 * 4 + 19  # graph epochs, plain windows (preconditioner updates) and a tail
-    if A == pet.SVRG:
+    if algo == "svrg":
         niter = 2 * 16 + 11  # several snapshot refreshes of every instance
+    elif algo == "svrg_bb":
+        # one BB step per instance (computed at its second refresh, k = 2n <= 16): a BB step
+        # is a ratio of dot products of differences of nearly equal images, so later steps
+        # amplify the atomics' rounding differences between the two runs
+        niter = 2 * 8 + 2
     solvers = [_solver(pet, p, plan, x0, 100 + i, A, rule) for i, (p, plan, _, _, x0) in enumerate(inst)]
     b = pet.Batch(solvers, iters_per_graph=E)
     b.run(niter)
