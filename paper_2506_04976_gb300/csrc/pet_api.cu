@@ -65,6 +65,8 @@ static void plan_free(pet_plan *p) {
   cudaFree(p->d_tof_grp2);
   cudaFree(p->d_tof_grp4);
   cudaFree(p->d_tof_work);
+  cudaFree(p->d_tof_xp);
+  cudaFree(p->d_tof_xtp);
   cudaFree(p->d_xs); cudaFree(p->d_rtmp);
   delete p;
 }
@@ -154,6 +156,14 @@ static pet_status build_tof_window(pet_plan *pl, const std::vector<float4> &plan
   dp.tof_grp4 = pl->d_tof_grp4;
   dp.tof_ngrp4 = (int)(grp4.size() / 4);
   dp.tof_work = pl->d_tof_work;
+  const size_t np = (size_t)(g.nz + 2 * kTofPad) * (g.ny * (size_t)(g.nx + 2 * kTofPad));
+  const size_t ntp = (size_t)(g.nz + 2 * kTofPad) * (g.nx * (size_t)(g.ny + 2 * kTofPad));
+  if (dalloc(&pl->d_tof_xp, np) != cudaSuccess || dalloc(&pl->d_tof_xtp, ntp) != cudaSuccess) return PET_ERR_NOMEM;
+  if (cudaMemset(pl->d_tof_xp, 0, np * sizeof(float)) != cudaSuccess ||
+      cudaMemset(pl->d_tof_xtp, 0, ntp * sizeof(float)) != cudaSuccess)
+    return PET_ERR_CUDA;
+  dp.tof_xp = pl->d_tof_xp;
+  dp.tof_xtp = pl->d_tof_xtp;
   int nsm = 0;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, pl->device) != cudaSuccess || nsm < 1)
     return PET_ERR_CUDA;

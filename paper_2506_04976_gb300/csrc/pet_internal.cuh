@@ -59,6 +59,7 @@ struct DevPlan {
   int tof_ngrp4;
   unsigned long long *tof_work;  // work counter of the persistent TOF kernel (plan scratch)
   int nsm;                       // multiprocessors of the plan's device
+  float *tof_xp, *tof_xtp;       // zero-padded image copies in the two view frames (plan scratch)
 };
 
 // Windowed TOF kernel constants: threads per block, table rows per bin width (a power of
@@ -67,6 +68,7 @@ constexpr int kTofBlock = 512;
 constexpr int kTofLogM = 10;
 constexpr int kTofM = 1 << kTofLogM;
 constexpr int kTofMaxBins = 16;
+constexpr int kTofPad = 2;  // zero voxels on each side of the b and z axes of the padded frames
 
 // Per-view data for the voxel-driven (deterministic) backprojector: fb0 is affine in
 // the radial index, fb0(v, r) ~ fbA + r fbB, used only to find candidate LORs.

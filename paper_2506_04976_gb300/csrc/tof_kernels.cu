@@ -162,7 +162,12 @@ __device__ __forceinline__ double tof_group(const DevPlan &P, const float4 *__re
     L.i1 = 0;
   }
   warp_uniform_range(L, ok);
-  const float *img = xdrive ? xT : x;
+  // the forward gathers from the zero-padded copy of the image in this view's frame
+  // (2 voxels of zeros on both sides of the b and z axes): indices clamped to the padding
+  // need no bounds tests, and samples outside the image read zeros
+  const float *imgp = xdrive ? P.tof_xtp : P.tof_xp;
+  const int Nbp = Nb + 2 * kTofPad;
+  const int planep = Na * Nbp;
   // window coordinate along the (possibly mirrored) LOR
   const bool mirror = dau < 0.f;
   const float sg = mirror ? -1.f : 1.f;
@@ -180,27 +185,24 @@ __device__ __forceinline__ double tof_group(const DevPlan &P, const float4 *__re
       if (!ok || i >= Na) continue;
       const float fb = fmaf((float)i, dfb, fb0);
       const float fbf = floorf(fb);
-      const int ib = (int)fbf;
+      const int ib = min(max((int)fbf, -kTofPad), Nb);
       const float wb = fb - fbf;
-      const bool b0 = (unsigned)ib < (unsigned)Nb;
-      const bool b1 = (unsigned)(ib + 1) < (unsigned)Nb && wb != 0.f;
-      const int row = i * Nb + ib;
+      const int rowp = i * Nbp + ib + kTofPad;
       float val[K];
       bool any = false;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const float fz = fmaf((float)i, dfz[k], fz0[k]);
         const float fzf = floorf(fz);
-        const int iz = (int)fzf;
+        const int iz = min(max((int)fzf, -kTofPad), P.nz);
         const float wz = fz - fzf;
-        const bool z0 = pv[k] && (unsigned)iz < (unsigned)P.nz;
-        const bool z1 = pv[k] && (unsigned)(iz + 1) < (unsigned)P.nz && wz != 0.f;
-        const int base = iz * plane + row;
-        const float v00 = (z0 && b0) ? __ldg(img + base) : 0.f;
-        const float v01 = (z0 && b1) ? __ldg(img + base + 1) : 0.f;
-        const float v10 = (z1 && b0) ? __ldg(img + base + plane) : 0.f;
-        const float v11 = (z1 && b1) ? __ldg(img + base + plane + 1) : 0.f;
-        val[k] = (1.f - wz) * ((1.f - wb) * v00 + wb * v01) + wz * ((1.f - wb) * v10 + wb * v11);
+        const int base = (iz + kTofPad) * planep + rowp;
+        const float v00 = __ldg(imgp + base);
+        const float v01 = __ldg(imgp + base + 1);
+        const float v10 = __ldg(imgp + base + planep);
+        const float v11 = __ldg(imgp + base + planep + 1);
+        const float v = (1.f - wz) * ((1.f - wb) * v00 + wb * v01) + wz * ((1.f - wb) * v10 + wb * v11);
+        val[k] = pv[k] ? v : 0.f;
         any |= val[k] != 0.f;
       }
       if (!any) continue;
@@ -529,9 +531,41 @@ static cudaError_t launch_tofk_k(const DevPlan &P, unsigned grid, int split, int
   return launch_tofk_w<K, 8>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
 }
 
+// Zero-padded copies of the image in both view frames: xp [nz+2p][ny][nx+2p] (views
+// driven along y) and xtp [nz+2p][nx][ny+2p] (views driven along x), p = kTofPad.  Only
+// the interior is written; the padding was cleared when the plan was created.  One
+// 32x32 tile of one slice per block, transposed through shared memory.
+__global__ void __launch_bounds__(256) k_pad_frames(const float *__restrict__ x, float *__restrict__ xp,
+                                                    float *__restrict__ xtp, int nx, int ny) {
+  __shared__ float tile[32][33];
+  const int z = blockIdx.z, x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const size_t sl = (size_t)z * nx * ny;
+  const size_t slp = (size_t)(z + kTofPad) * ny * (nx + 2 * kTofPad);
+  const size_t sltp = (size_t)(z + kTofPad) * nx * (ny + 2 * kTofPad);
+  for (int j = ty; j < 32; j += 8) {
+    const int xx = x0 + tx, yy = y0 + j;
+    if (xx < nx && yy < ny) {
+      const float v = x[sl + (size_t)yy * nx + xx];
+      xp[slp + (size_t)yy * (nx + 2 * kTofPad) + xx + kTofPad] = v;
+      tile[j][tx] = v;
+    }
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int xx = x0 + j, yy = y0 + tx;
+    if (xx < nx && yy < ny) xtp[sltp + (size_t)xx * (ny + 2 * kTofPad) + yy + kTofPad] = tile[tx][j];
+  }
+}
+
 cudaError_t launch_grad_tofk(const DevPlan &P, int K, int split, unsigned grid, int subset, const int *subset_dev,
                              const float *x, const float *xT, float *g, float *gT, double *kl_part, int mode,
                              cudaStream_t st) {
+  if (mode != MODE_SENS) {
+    note_launch();
+    k_pad_frames<<<dim3((P.nx + 31) / 32, (P.ny + 31) / 32, P.nz), dim3(32, 8), 0, st>>>(x, P.tof_xp, P.tof_xtp,
+                                                                                         P.nx, P.ny);
+  }
   note_launch();
   if (K == 4) return launch_tofk_k<4>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
   if (K == 2) return launch_tofk_k<2>(P, grid, split, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
