@@ -105,6 +105,7 @@ def test_c4_batch_of_32_matches_single_runs_and_oracle():
     subs_b = [s.subsets() for s in solvers]
     del b, solvers
     for i, (p, plan, _, _, x0) in enumerate(inst):
+        plan.set_grad_shape(2, 1)  # the batch's launch shape: only the atomics' order differs
         s1 = _saga(pet, p, plan, x0, 500 + i)
         s1.run(niter)
         torch.cuda.synchronize()
