@@ -819,21 +819,26 @@ def measure_svrg(pet, dev, cfg, p, dt, args, rank, world, pg, e2e=True, clk=None
         xo = torch.empty(plan.img_shape, pin_memory=True)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         a.record()
-        for _ in range(args.steps):
+        for i in range(args.steps):
+            cp[i][0].record()
             dt["y"].copy_(y_host, non_blocking=True)
             dt["r"].copy_(r_host, non_blocking=True)
             x_dev.copy_(x0_host, non_blocking=True)
+            cp[i][1].record()
             solver.set_image(x_dev)
             solver.run(step_len)
             xo.copy_(solver.image(), non_blocking=True)
         b.record()
         torch.cuda.synchronize()
         te = max_over_ranks(pg, a.elapsed_time(b) / 1e3, dev)
+        h2d_ms = sum(c0.elapsed_time(c1) for c0, c1 in cp) / args.steps
         out["e2e"] = {"value": whole_job_rate(grads_per_step * args.steps, world, te), "unit": UNIT,
                       "h2d_bytes_per_step": int(y_host.numel() * y_host.element_size() + r_host.numel() * 4 +
                                                 x0_host.numel() * 4),
-                      "d2h_bytes_per_step": int(xo.numel() * 4)}
+                      "d2h_bytes_per_step": int(xo.numel() * 4), "ms_per_step": 1e3 * te / args.steps,
+                      "h2d_ms_per_step": h2d_ms}
         solver.kernel_time()
         del y_host, r_host
     del solver, plan
