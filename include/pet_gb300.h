@@ -123,9 +123,16 @@ const float *pet_plan_sensitivity(const pet_plan *plan, int subset);
 pet_status pet_plan_set_grad_shape(pet_plan *plan, int planes_per_thread, int parts);
 
 /* Autotuner: times every valid launch shape on subset 0 of the bound data (a uniform
- * image), keeps the fastest in the plan and returns it.  Uses plan scratch; synchronises
- * `stream`.  Requires pet_plan_set_data. */
+ * image), keeps the fastest in the plan and returns it; also times the RDP stencil tile
+ * (32 x 8 voxels x 2, 4 or 8 slices per block) on the plan's image and keeps the fastest
+ * for the plan's prior evaluations (solvers, pet_objective_grad).  Uses plan scratch;
+ * synchronises `stream`.  Requires pet_plan_set_data. */
 pet_status pet_plan_autotune(pet_plan *plan, void *stream, int *planes_per_thread, int *parts);
+
+/* RDP stencil tile of the plan's prior evaluations: 2, 4 or 8 slices per block of 32 x 8
+ * voxels (0 = the default, 4).  Results are identical for every tile.  PET_ERR_ARG for
+ * other values. */
+pet_status pet_plan_set_rdp_tile(pet_plan *plan, int slices);
 
 /* Reads and clears the device error word after synchronising `stream`: PET_OK or
  * PET_ERR_INFEASIBLE. */
@@ -304,8 +311,8 @@ void pet_batch_destroy(pet_batch *b);
 /* Runs niter iterations of every solver (each solver's iteration counter advances). */
 pet_status pet_batch_run(pet_batch *b, long long niter, void *stream);
 /* Launch shape of the batched fused gradient (planes per thread 1, 2 or 4; parts per
- * LOR 1, 2, 4 or 8) and its autotuner (times each shape on subset 0 of every solver;
- * synchronises stream). */
+ * LOR 1, 2, 4 or 8) and its autotuner (times each shape on subset 0 of every solver, then
+ * the batched RDP stencil tile of 2, 4 or 8 slices per block; synchronises stream). */
 pet_status pet_batch_set_grad_shape(pet_batch *b, int planes_per_thread, int parts);
 pet_status pet_batch_autotune(pet_batch *b, void *stream, int *planes_per_thread, int *parts);
 

@@ -90,6 +90,7 @@ _sigs = {
     "pet_plan_check": (C.c_int, [_vp, _vp]),
     "pet_plan_set_grad_shape": (C.c_int, [_vp, C.c_int, C.c_int]),
     "pet_plan_autotune": (C.c_int, [_vp, _vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "pet_plan_set_rdp_tile": (C.c_int, [_vp, C.c_int]),
     "pet_forward": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
     "pet_back": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, _vp]),
     "pet_objective_grad": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, C.POINTER(RdpParams), C.c_int, _vp]),
@@ -217,8 +218,13 @@ class Plan:
         _ck(_lib.pet_plan_set_grad_shape(self._h, int(planes_per_thread), int(parts)),
             "pet_plan_set_grad_shape")
 
+    def set_rdp_tile(self, slices=0):
+        """RDP stencil tile of the plan's prior evaluations: 2, 4 or 8 slices (0: default)."""
+        _ck(_lib.pet_plan_set_rdp_tile(self._h, int(slices)), "pet_plan_set_rdp_tile")
+
     def autotune(self):
-        """Times the fused-gradient launch shapes and keeps the fastest; returns it."""
+        """Times the fused-gradient launch shapes and the RDP stencil tiles and keeps the
+        fastest; returns the gradient's shape."""
         k, sp = C.c_int(), C.c_int()
         _ck(_lib.pet_plan_autotune(self._h, _stream(), C.byref(k), C.byref(sp)), "pet_plan_autotune")
         return k.value, sp.value

@@ -10,7 +10,9 @@
 
 namespace petgb {
 
-constexpr int RDP_TX = 32, RDP_TY = 8, RDP_ZCH = 4;  // tile: 32 x 8 voxels x 4 slices
+// tile: 32 x 8 voxels x zch slices (zch = 2, 4 or 8, chosen per image by the autotuners;
+// default 4); the shared-memory planes are sized for the largest
+constexpr int RDP_TX = 32, RDP_TY = 8, RDP_ZMAX = 8;
 
 RdpArgs make_rdp_args(const pet_rdp_params &p) {
   RdpArgs a;
@@ -22,11 +24,13 @@ RdpArgs make_rdp_args(const pet_rdp_params &p) {
     a.w[k] = (float)(dmin / sqrt(ex * ex + ey * ey + ez * ez));
   }
   a.gamma = p.gamma; a.eps = p.eps; a.scale = p.scale; a.kappa = p.kappa;
+  a.zch = kRdpZchDefault;
   return a;
 }
 
-int rdp_blocks(int nx, int ny, int nz) {
-  return ((nx + RDP_TX - 1) / RDP_TX) * ((ny + RDP_TY - 1) / RDP_TY) * ((nz + RDP_ZCH - 1) / RDP_ZCH);
+int rdp_blocks(int nx, int ny, int nz, int zch) {
+  zch = rdp_zch_valid(zch);
+  return ((nx + RDP_TX - 1) / RDP_TX) * ((ny + RDP_TY - 1) / RDP_TY) * ((nz + zch - 1) / zch);
 }
 
 __device__ __forceinline__ double block_sum_d(double v) {
@@ -87,24 +91,24 @@ __device__ __forceinline__ void rdp_voxel(const RdpArgs &a, const float (*sx)[RD
   }
 }
 
-// One block: a 32x8 tile over RDP_ZCH slices.  All RDP_ZCH + 2 planes (with halo) are
-// staged in shared memory at once, then every slice is computed without further
-// barriers.
+// One block: a 32x8 tile over a.zch slices.  All zch + 2 planes (with halo) are staged in
+// shared memory at once, then every slice is computed without further barriers.
 template <bool KAPPA, bool WG, bool WH, bool VAL>
 __device__ __forceinline__ void rdp_body(const RdpArgs &a, const float *__restrict__ x, float *__restrict__ grad,
                                          float *__restrict__ hdiag, double *__restrict__ val_out, int accumulate,
                                          int blk) {
-  __shared__ float sx[RDP_ZCH + 2][RDP_TY + 2][RDP_TX + 2];
-  __shared__ float sk[KAPPA ? RDP_ZCH + 2 : 1][RDP_TY + 2][RDP_TX + 2];
+  __shared__ float sx[RDP_ZMAX + 2][RDP_TY + 2][RDP_TX + 2];
+  __shared__ float sk[KAPPA ? RDP_ZMAX + 2 : 1][RDP_TY + 2][RDP_TX + 2];
+  const int zch = rdp_zch_valid(a.zch);
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * RDP_TX + tx;
   const int nbx = (a.nx + RDP_TX - 1) / RDP_TX, nby = (a.ny + RDP_TY - 1) / RDP_TY;
   const int bx = blk % nbx, by = (blk / nbx) % nby, bz = blk / (nbx * nby);
   const int x0 = bx * RDP_TX, y0 = by * RDP_TY;
-  const int z0 = bz * RDP_ZCH, z1 = min(a.nz, z0 + RDP_ZCH);
+  const int z0 = bz * zch, z1 = min(a.nz, z0 + zch);
   const int nxy = a.nx * a.ny;
   const bool inner_xy = x0 >= 1 && x0 + RDP_TX < a.nx && y0 >= 1 && y0 + RDP_TY < a.ny;
   constexpr int PLANE = (RDP_TY + 2) * (RDP_TX + 2);
-  for (int e = tid; e < (RDP_ZCH + 2) * PLANE; e += RDP_TX * RDP_TY) {
+  for (int e = tid; e < (zch + 2) * PLANE; e += RDP_TX * RDP_TY) {
     const int lz = e / PLANE, rem = e % PLANE;
     const int ly = rem / (RDP_TX + 2), lx = rem % (RDP_TX + 2);
     const int z = z0 + lz - 1, gx = x0 + lx - 1, gy = y0 + ly - 1;
@@ -197,7 +201,7 @@ static void rdp_dispatch(const RdpArgs &a, int nb, dim3 block, const float *x, f
 
 cudaError_t launch_rdp(const RdpArgs &a, const float *x, float *grad, float *hdiag,
                        double *val_part, int accumulate, int *nblocks_out, cudaStream_t st) {
-  const int nb = rdp_blocks(a.nx, a.ny, a.nz);
+  const int nb = rdp_blocks(a.nx, a.ny, a.nz, a.zch);
   if (nblocks_out) *nblocks_out = nb;
   if (!grad && !hdiag && !val_part) return cudaSuccess;
   dim3 block(RDP_TX, RDP_TY);

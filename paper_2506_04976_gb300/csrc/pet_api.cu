@@ -256,7 +256,7 @@ extern "C" pet_status pet_plan_create(const pet_geometry *geom, pet_plan **out) 
   // any fused-gradient launch (up to 16 parts per LOR) has at most this many blocks
   const int gb_all = (int)((16 * nlor + kBlock - 1) / kBlock) + 1;
   const int rb = ratio_blocks(dp, -1);
-  pl->npart = std::max({gb_all, rb, rdp_blocks(g.nx, g.ny, g.nz), 4 * nrmse_blocks(pl->N), 1});
+  pl->npart = std::max({gb_all, rb, rdp_blocks(g.nx, g.ny, g.nz, 2), 4 * nrmse_blocks(pl->N), 1});
   bool ok = dalloc(&pl->d_view, V) == cudaSuccess && dalloc(&pl->d_vr, (size_t)V * R) == cudaSuccess &&
             dalloc(&pl->d_plane, P) == cudaSuccess && dalloc(&pl->d_aff, V) == cudaSuccess &&
             dalloc(&pl->d_m, (size_t)nlor) == cudaSuccess && dalloc(&pl->d_sens, pl->N) == cudaSuccess &&
@@ -489,6 +489,7 @@ extern "C" pet_status pet_objective_grad(pet_plan *plan, int subset, const float
   if (obj) PET_CK(launch_reduce_sum(plan->d_part, nparts, obj, 0, st));
   if (prior) {
     RdpArgs a = make_rdp_args(*prior);
+    a.zch = plan->rdp_zch;
     int nb = 0;
     PET_CK(launch_rdp(a, x, obj_only ? nullptr : g, nullptr, obj ? plan->d_part : nullptr, 1, &nb, st));
     if (obj) PET_CK(launch_reduce_sum(plan->d_part, nb, obj, 1, st));
@@ -559,6 +560,12 @@ extern "C" pet_status pet_plan_set_grad_shape(pet_plan *plan, int planes_per_thr
   return PET_OK;
 }
 
+extern "C" pet_status pet_plan_set_rdp_tile(pet_plan *plan, int slices) {
+  if (!plan || !(slices == 0 || slices == 2 || slices == 4 || slices == 8)) return PET_ERR_ARG;
+  plan->rdp_zch = slices ? slices : kRdpZchDefault;
+  return PET_OK;
+}
+
 extern "C" pet_status pet_plan_autotune(pet_plan *plan, void *stream, int *planes_per_thread, int *parts) {
   if (!plan) return PET_ERR_ARG;
   if (!plan->has_data) return PET_ERR_STATE;
@@ -614,6 +621,30 @@ extern "C" pet_status pet_plan_autotune(pet_plan *plan, void *stream, int *plane
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 5; ++b)
       if (tmin[a][b] < best) { best = tmin[a][b]; bk = ks[a]; bs = ss[b]; }
+  // RDP stencil tile: slices per block, timed on the same image (gradient only)
+  pet_rdp_params rp = {};
+  rp.nx = plan->g.nx; rp.ny = plan->g.ny; rp.nz = plan->g.nz;
+  rp.dx = plan->g.dx; rp.dy = plan->g.dy; rp.dz = plan->g.dz;
+  rp.gamma = 2.f; rp.eps = 1e-3f; rp.scale = 1.f; rp.kappa = nullptr;
+  RdpArgs ra = make_rdp_args(rp);
+  const int zs[3] = {2, 4, 8};
+  float zbest = 1e30f;
+  int bz = kRdpZchDefault;
+  for (int round = 0; round < 2; ++round)
+    for (int zch : zs) {
+      ra.zch = zch;
+      float ms = 0.f;
+      bool fail = false;
+      for (int it = 0; it < 12 && !fail; ++it) {
+        if (it == 2) fail |= cudaEventRecord(e0, st) != cudaSuccess;
+        fail |= launch_rdp(ra, x, g, nullptr, nullptr, 0, nullptr, st) != cudaSuccess;
+      }
+      fail |= cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess;
+      if (fail) break;
+      if (ms < zbest) { zbest = ms; bz = zch; }
+    }
+  plan->rdp_zch = bz;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamSynchronize(st);

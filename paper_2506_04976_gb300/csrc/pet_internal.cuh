@@ -285,11 +285,19 @@ struct RdpArgs {
   float w[7];  // weights for offsets (1,0,0),(0,1,0),(0,0,1),(1,1,0),(1,0,1),(0,1,1),(1,1,1)
   float gamma, eps, scale;
   const float *kappa;
+  int zch;  // slices per stencil block: 2, 4 or 8
 };
+constexpr int kRdpZchDefault = 4;
+// The slice count a stencil launch uses: 2, 4 or 8 (anything else falls back to 4), so
+// that the block count and the kernel's shared-memory planes always agree.
+__host__ __device__ __forceinline__ int rdp_zch_valid(int zch) {
+  return (zch == 2 || zch == 4 || zch == 8) ? zch : kRdpZchDefault;
+}
 RdpArgs make_rdp_args(const pet_rdp_params &p);
 cudaError_t launch_rdp(const RdpArgs &a, const float *x, float *grad, float *hdiag,
                        double *val_part, int accumulate, int *nblocks_out, cudaStream_t st);
-int rdp_blocks(int nx, int ny, int nz);
+// Stencil blocks of an image with zch slices per block (the default tile unless given).
+int rdp_blocks(int nx, int ny, int nz, int zch = kRdpZchDefault);
 struct RdpJob {
   RdpArgs a;
   const float *x;

@@ -12,6 +12,7 @@ struct pet_plan {
   int T = 1;                  // TOF bins (1: non-TOF)
   int vs_max = 0;             // views in the largest subset
   int device = 0;
+  int rdp_zch = petgb::kRdpZchDefault;  // slices per RDP stencil block (autotuned)
   bool has_data = false;
   petgb::DevPlan dp;
   petgb::DevPlanDet dd;

@@ -809,7 +809,9 @@ static RdpArgs prior_args(const pet_solver *s, float scale) {
   rp.nx = s->plan->g.nx; rp.ny = s->plan->g.ny; rp.nz = s->plan->g.nz;
   rp.dx = s->plan->g.dx; rp.dy = s->plan->g.dy; rp.dz = s->plan->g.dz;
   rp.gamma = s->o.gamma; rp.eps = s->o.eps; rp.scale = scale; rp.kappa = s->o.kappa;
-  return make_rdp_args(rp);
+  RdpArgs a = make_rdp_args(rp);
+  a.zch = s->plan->rdp_zch;
+  return a;
 }
 
 // grad S(x) into gS on the side stream, ordered after everything enqueued on st so far;
@@ -1119,6 +1121,7 @@ struct pet_batch {
   cudaStream_t side = nullptr;  // the prior's gradients, concurrent with the subset gradients
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::vector<char> after_single;  // instance ran its last iteration alone (accumulators to clear)
+  int rdp_zch = 0;                 // slices per batched RDP stencil block (0: each plan's own)
 };
 
 static void batch_free(pet_batch *b) {
@@ -1220,7 +1223,8 @@ static pet_status batch_tables(pet_batch *b) {
     cj[i].b = p->d_gT;
     cj[i].N = s->N;
     gb[i + 1] = gb[i] + grad_blocks_shape(p->dp, p->vs_max, b->K, b->split);
-    rb[i + 1] = rb[i] + rdp_blocks(p->g.nx, p->g.ny, p->g.nz);
+    if (b->rdp_zch) rj[i].a.zch = b->rdp_zch;
+    rb[i + 1] = rb[i] + rdp_blocks(p->g.nx, p->g.ny, p->g.nz, rj[i].a.zch);
     ub[i + 1] = ub[i] + ((p->g.nx + 31) / 32) * ((p->g.ny + 31) / 32) * p->g.nz;
     cb[i + 1] = cb[i] + (int)std::max<size_t>(1, std::min<size_t>(256, (s->N / 4 + 255) / 256));
   }
@@ -1327,6 +1331,28 @@ extern "C" pet_status pet_batch_autotune(pet_batch *b, void *stream, int *planes
   for (int a = 0; a < 3; ++a)
     for (int c = 0; c < 4; ++c)
       if (tmin[a][c] < best) { best = tmin[a][c]; bk = ks[a]; bs = ss[c]; }
+  // RDP stencil tile of the batched prior launch (slices per block, one for all instances)
+  const int zs[3] = {2, 4, 8};
+  float zbest = 1e30f;
+  int bz = kRdpZchDefault;
+  for (int round = 0; round < 2 && e == PET_OK; ++round)
+    for (int zch : zs) {
+      b->rdp_zch = zch;
+      e = batch_tables(b);
+      if (e != PET_OK) break;
+      float ms = 0.f;
+      for (int it = 0; it < 10; ++it) {
+        if (it == 2) cudaEventRecord(e0, st);
+        launch_rdp_batch(b->d_rjobs, b->d_rbegin, b->nj, b->rblocks, nullptr, st);
+      }
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        e = PET_ERR_CUDA;
+        break;
+      }
+      if (ms < zbest) { zbest = ms; bz = zch; }
+    }
+  b->rdp_zch = bz;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->K = bk;

@@ -376,6 +376,26 @@ def test_grad_launch_shapes(key, shape):
         c.plan.set_grad_shape(0, 0)
 
 
+@pytest.mark.parametrize("slices", [2, 4, 8])
+def test_rdp_tiles_in_the_subset_objective(slices):
+    """Every RDP stencil tile (slices per block) gives the oracle's prior share of the
+    subset objective and gradient (eq. 5)."""
+    c = case("3d")
+    c.plan.set_rdp_tile(slices)
+    try:
+        s, beta, gam, eps = 2, 0.3, 2.0, 1e-3
+        obj, g = c.plan.objective_grad(c.xt, s, prior=(beta / c.n, gam, eps))
+        val, gd = O.data_grad(c.G, c.n, s, c.x, c.m, c.p["r"], c.p["y"])
+        S, gs, _ = O.rdp(c.x.astype(np.float64), (c.g["dx"], c.g["dy"], c.g["dz"]), gam, eps)
+        scale = O.sensitivity(c.G, c.n, s, c.m)
+        d = np.abs(g.cpu().numpy() - (gd + beta / c.n * gs))
+        assert np.linalg.norm(d) <= 1e-5 * np.linalg.norm(scale)
+        f = val + beta / c.n * S
+        assert abs(float(obj) - f) <= 1e-5 * abs(f)
+    finally:
+        c.plan.set_rdp_tile(0)
+
+
 def test_autotune_keeps_parity():
     c = case("3d")
     k, parts = c.plan.autotune()
