@@ -67,6 +67,8 @@ static void plan_free(pet_plan *p) {
   cudaFree(p->d_tof_work);
   cudaFree(p->d_tof_xp);
   cudaFree(p->d_tof_xtp);
+  cudaFree(p->d_tof_gp);
+  cudaFree(p->d_tof_gtp);
   cudaFree(p->d_xs); cudaFree(p->d_rtmp);
   delete p;
 }
@@ -158,12 +160,18 @@ static pet_status build_tof_window(pet_plan *pl, const std::vector<float4> &plan
   dp.tof_work = pl->d_tof_work;
   const size_t np = (size_t)(g.nz + 2 * kTofPad) * (g.ny * (size_t)(g.nx + 2 * kTofPad));
   const size_t ntp = (size_t)(g.nz + 2 * kTofPad) * (g.nx * (size_t)(g.ny + 2 * kTofPad));
-  if (dalloc(&pl->d_tof_xp, np) != cudaSuccess || dalloc(&pl->d_tof_xtp, ntp) != cudaSuccess) return PET_ERR_NOMEM;
+  if (dalloc(&pl->d_tof_xp, np) != cudaSuccess || dalloc(&pl->d_tof_xtp, ntp) != cudaSuccess ||
+      dalloc(&pl->d_tof_gp, np) != cudaSuccess || dalloc(&pl->d_tof_gtp, ntp) != cudaSuccess)
+    return PET_ERR_NOMEM;
   if (cudaMemset(pl->d_tof_xp, 0, np * sizeof(float)) != cudaSuccess ||
-      cudaMemset(pl->d_tof_xtp, 0, ntp * sizeof(float)) != cudaSuccess)
+      cudaMemset(pl->d_tof_xtp, 0, ntp * sizeof(float)) != cudaSuccess ||
+      cudaMemset(pl->d_tof_gp, 0, np * sizeof(float)) != cudaSuccess ||
+      cudaMemset(pl->d_tof_gtp, 0, ntp * sizeof(float)) != cudaSuccess)
     return PET_ERR_CUDA;
   dp.tof_xp = pl->d_tof_xp;
   dp.tof_xtp = pl->d_tof_xtp;
+  dp.tof_gp = pl->d_tof_gp;
+  dp.tof_gtp = pl->d_tof_gtp;
   int nsm = 0;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, pl->device) != cudaSuccess || nsm < 1)
     return PET_ERR_CUDA;

@@ -60,6 +60,7 @@ struct DevPlan {
   unsigned long long *tof_work;  // work counter of the persistent TOF kernel (plan scratch)
   int nsm;                       // multiprocessors of the plan's device
   float *tof_xp, *tof_xtp;       // zero-padded image copies in the two view frames (plan scratch)
+  float *tof_gp, *tof_gtp;       // zero-padded gradient accumulators in the two view frames
 };
 
 // Windowed TOF kernel constants: threads per block, table rows per bin width (a power of

@@ -28,6 +28,7 @@ struct pet_plan {
   int *d_tof_grp4 = nullptr;    // TOF: plane quadruples of equal axial slope
   unsigned long long *d_tof_work = nullptr;  // TOF: work counter of the persistent kernel
   float *d_tof_xp = nullptr, *d_tof_xtp = nullptr;  // TOF: zero-padded image frames
+  float *d_tof_gp = nullptr, *d_tof_gtp = nullptr;  // TOF: zero-padded gradient accumulators
   // derived data
   float *d_m = nullptr;         // [V][P][R] multiplicative factors
   float *d_sens = nullptr;      // [N] A^T 1

@@ -127,7 +127,6 @@ __device__ __forceinline__ double tof_group(const DevPlan &P, const float4 *__re
   const float g1 = dau * inv2h, g2 = t0b * inv2h;
   const int Na = xdrive ? P.nx : P.ny;
   const int Nb = xdrive ? P.ny : P.nx;
-  const int plane = Na * Nb;
   int pk[K];
   bool pv[K];
   float fz0[K], dfz[K];
@@ -292,7 +291,9 @@ __device__ __forceinline__ double tof_group(const DevPlan &P, const float4 *__re
   }
 
   if (mode != MODE_OBJ) {
-    float *out = xdrive ? gT : g;
+    // the scatter goes to zero-padded accumulators in the view's frame (neighbours outside
+    // the image land in the padding, which the combine pass after the kernel discards)
+    float *outp = xdrive ? P.tof_gtp : P.tof_gp;
     float2 qw[K][WP];
     int kbase = INT_MIN;
     for (int i = L.i0 + part; i <= L.i1; i += SPLIT) {
@@ -327,9 +328,8 @@ __device__ __forceinline__ double tof_group(const DevPlan &P, const float4 *__re
       const float fbf = floorf(fb);
       const int ib = (int)fbf;
       const float wb = fb - fbf;
-      const bool b0 = (unsigned)ib < (unsigned)Nb;
-      const bool b1 = (unsigned)(ib + 1) < (unsigned)Nb && wb != 0.f;
-      const int row = i * Nb + ib;
+      if ((unsigned)(ib + 1) > (unsigned)Nb) continue;  // both in-plane neighbours outside
+      const int rowp = i * Nbp + ib + kTofPad;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         if (val[k] == 0.f) continue;
@@ -337,14 +337,15 @@ __device__ __forceinline__ double tof_group(const DevPlan &P, const float4 *__re
         const float fzf = floorf(fz);
         const int iz = (int)fzf;
         const float wz = fz - fzf;
-        const bool z0 = (unsigned)iz < (unsigned)P.nz;
-        const bool z1 = (unsigned)(iz + 1) < (unsigned)P.nz && wz != 0.f;
-        const int base = iz * plane + row;
+        if ((unsigned)(iz + 1) > (unsigned)P.nz) continue;  // both axial neighbours outside
+        const int base = (iz + kTofPad) * planep + rowp;
         const float a0 = (1.f - wz) * val[k], a1 = wz * val[k];
-        if (z0 && b0) atomicAdd(out + base, (1.f - wb) * a0);
-        if (z0 && b1) atomicAdd(out + base + 1, wb * a0);
-        if (z1 && b0) atomicAdd(out + base + plane, (1.f - wb) * a1);
-        if (z1 && b1) atomicAdd(out + base + plane + 1, wb * a1);
+        atomicAdd(outp + base, (1.f - wb) * a0);
+        atomicAdd(outp + base + 1, wb * a0);
+        if (wz != 0.f) {  // the upper row of a plane through slice centres has weight 0
+          atomicAdd(outp + base + planep, (1.f - wb) * a1);
+          atomicAdd(outp + base + planep + 1, wb * a1);
+        }
       }
     }
   }
@@ -558,9 +559,54 @@ __global__ void __launch_bounds__(256) k_pad_frames(const float *__restrict__ x,
   }
 }
 
+static cudaError_t launch_grad_tofk_core(const DevPlan &P, int K, int split, unsigned grid, int subset,
+                                         const int *subset_dev, const float *x, const float *xT, float *g, float *gT,
+                                         double *kl_part, int mode, cudaStream_t st);
+
+// g += the interiors of the padded accumulators (gtp transposed back through shared
+// memory); the caller then clears both padded arrays, padding included.
+__global__ void __launch_bounds__(256) k_unpad_add(const float *__restrict__ gp, const float *__restrict__ gtp,
+                                                   float *__restrict__ g, int nx, int ny) {
+  __shared__ float tile[32][33];
+  const int z = blockIdx.z, x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const size_t sl = (size_t)z * nx * ny;
+  const size_t slp = (size_t)(z + kTofPad) * ny * (nx + 2 * kTofPad);
+  const size_t sltp = (size_t)(z + kTofPad) * nx * (ny + 2 * kTofPad);
+  for (int j = ty; j < 32; j += 8) {
+    const int xx = x0 + j, yy = y0 + tx;
+    if (xx < nx && yy < ny) tile[j][tx] = gtp[sltp + (size_t)xx * (ny + 2 * kTofPad) + yy + kTofPad];
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int xx = x0 + tx, yy = y0 + j;
+    if (xx < nx && yy < ny) {
+      const size_t i = sl + (size_t)yy * nx + xx;
+      g[i] += gp[slp + (size_t)yy * (nx + 2 * kTofPad) + xx + kTofPad] + tile[tx][j];
+    }
+  }
+}
+
 cudaError_t launch_grad_tofk(const DevPlan &P, int K, int split, unsigned grid, int subset, const int *subset_dev,
                              const float *x, const float *xT, float *g, float *gT, double *kl_part, int mode,
                              cudaStream_t st) {
+  cudaError_t e = launch_grad_tofk_core(P, K, split, grid, subset, subset_dev, x, xT, g, gT, kl_part, mode, st);
+  if (e != cudaSuccess || mode == MODE_OBJ) return e;
+  const dim3 tiles((P.nx + 31) / 32, (P.ny + 31) / 32, P.nz);
+  note_launch();
+  k_unpad_add<<<tiles, dim3(32, 8), 0, st>>>(P.tof_gp, P.tof_gtp, g, P.nx, P.ny);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t np = (size_t)(P.nz + 2 * kTofPad) * P.ny * (P.nx + 2 * kTofPad);
+  const size_t ntp = (size_t)(P.nz + 2 * kTofPad) * P.nx * (P.ny + 2 * kTofPad);
+  e = cudaMemsetAsync(P.tof_gp, 0, np * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.tof_gtp, 0, ntp * sizeof(float), st);
+  return e;
+}
+
+static cudaError_t launch_grad_tofk_core(const DevPlan &P, int K, int split, unsigned grid, int subset,
+                                         const int *subset_dev, const float *x, const float *xT, float *g, float *gT,
+                                         double *kl_part, int mode, cudaStream_t st) {
   if (mode != MODE_SENS) {
     note_launch();
     k_pad_frames<<<dim3((P.nx + 31) / 32, (P.ny + 31) / 32, P.nz), dim3(32, 8), 0, st>>>(x, P.tof_xp, P.tof_xtp,
