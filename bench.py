@@ -731,7 +731,11 @@ def kernel_name(geom, shape):
     if T > 1:
         win = tof_window(geom)
         if T <= 16 and win <= 8:
-            return f"k_grad_tofk<{shape[0]},{4 if win <= 4 else 6 if win <= 6 else 8},{shape[1]}>"
+            wk = 4 if win <= 4 else 6 if win <= 6 else 8
+            nt = 256 if shape[0] == 4 else 512
+            if shape[1] == 1:  # one part per LOR: the persistent form
+                return f"k_grad_tofp<{shape[0]},{wk},{nt}>"
+            return f"k_grad_tofk<{shape[0]},{wk},{shape[1]},{nt}>"
         return f"k_grad<{16 if T <= 16 else 32},{shape[1]}>"
     return f"k_grad_mp<{shape[0]},{shape[1]}>" if shape[0] > 1 else f"k_grad<1,{shape[1]}>"
 
