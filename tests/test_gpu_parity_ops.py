@@ -4,7 +4,8 @@ Tolerances (derived from FP32 arithmetic):
   * projections, backprojections, sensitivities, attenuation factors: relative L2 error
     per view / per image <= 1e-5 and elementwise |d| <= 1e-4 |ref| + 1e-5 max|ref|;
   * gradients of the KL term (a difference of two positive backprojections): errors
-    measured against the scale of A^T 1;
+    measured against the scale of A^T 1, in L2 (1e-5 of ||A_s^T 1||) and per voxel
+    (1e-4 (A_s^T 1)_j + 1e-6 max A_s^T 1, which also bounds entries near zero);
   * RDP: max-norm relative 1e-5 (gradient), elementwise 1e-5 (Hessian diagonal),
     1e-5 (value); KL objective 1e-5 relative;
   * sums of many FP32 atomics: adjointness within 1e-5 relative.
@@ -147,6 +148,7 @@ def test_subset_objective_and_gradient(key, det):
     d = np.abs(g - ref)
     assert np.linalg.norm(d) <= 1e-5 * np.linalg.norm(scale)
     assert d.max() <= 1e-4 * scale.max()
+    assert np.all(d <= 1e-4 * scale + 1e-6 * scale.max())  # per voxel, small entries included
     f = val + beta / c.n * S
     assert abs(float(obj) - f) <= 1e-5 * abs(f)
     c.plan.check()
@@ -208,6 +210,7 @@ def test_full_size_c2_sampled_rows_and_subset_gradient():
     scale = O.sensitivity(G, p["nsub"], s, m)
     d = np.abs(gg.cpu().numpy() - gd)
     assert np.linalg.norm(d) <= 1e-5 * np.linalg.norm(scale)
+    assert np.all(d <= 1e-4 * scale + 1e-6 * scale.max())  # per voxel, small entries included
 
 
 def test_full_size_c3_sampled_tof_lors_and_subset_gradient():
@@ -243,7 +246,9 @@ def test_full_size_c3_sampled_tof_lors_and_subset_gradient():
     obj, gg = plan.objective_grad(xt, s)
     val, gd = O.data_grad(G, p["nsub"], s, x, m, p["r"], p["y"])
     scale = O.sensitivity(G, p["nsub"], s, m)
-    assert np.linalg.norm(gg.cpu().numpy() - gd) <= 1e-5 * np.linalg.norm(scale)
+    d = np.abs(gg.cpu().numpy() - gd)
+    assert np.linalg.norm(d) <= 1e-5 * np.linalg.norm(scale)
+    assert np.all(d <= 1e-4 * scale + 1e-6 * scale.max())  # per voxel, small entries included
     assert abs(float(obj) - val) <= 1e-5 * abs(val)
 
 
