@@ -70,6 +70,8 @@ def parse():
                     help="study mode: workload with a converged reference image in tests/golden")
     ap.add_argument("--study-nsub", type=int, default=0,
                     help="study mode: number of subsets (0: the workload's own; Sec. 3.2 uses 27)")
+    ap.add_argument("--study-plain", action="store_true",
+                    help="study mode: the plain form (one launch per kernel, no CUDA graphs)")
     return ap.parse_args()
 
 
@@ -515,15 +517,16 @@ def run_study(args, pet, dev, max_epochs=1500):
             for tau0 in (0.3, 1.0, 1.5):
                 solver = pet.Solver(plan, algo=algo, omega=2, step_rule=pet.STEP_VANISH, tau0=tau0, eta=0.02,
                                     precond_kind=pc, pc_iters=(0, n, 2 * n), beta=p["beta"], gamma=p["gamma"],
-                                    eps=p["eps"], seed=31)
+                                    eps=p["eps"], seed=31, use_graph=not args.study_plain)
                 rows.append({"algo": aname, "precond": pname, "tau0": tau0, **until_1pct(solver)})
                 del solver
     for name in ("ALG1", "ALG2", "ALG3"):  # the submitted algorithms (Table 1) with this n
         solver = pet.Solver(plan, beta=p["beta"], gamma=p["gamma"], eps=p["eps"], seed=31,
-                            **petric_solver_kwargs(name, n))
+                            use_graph=not args.study_plain, **petric_solver_kwargs(name, n))
         rows.append({"algo": name, "precond": "harmonic", "tau0": None, **until_1pct(solver)})
         del solver
     print(json.dumps({"mode": "study", "workload": f"{cfg}, n = {n}, beta = {p['beta']:.4g}", "max_epochs": max_epochs,
+                      "form": "plain" if args.study_plain else "graph",
                       "reference_kkt": float(ref["kkt"]), "runs": rows}), flush=True)
 
 
