@@ -122,8 +122,8 @@ const float *pet_plan_sensitivity(const pet_plan *plan, int subset);
  * the same up to FP32 summation order.  PET_ERR_ARG for an unsupported shape. */
 pet_status pet_plan_set_grad_shape(pet_plan *plan, int planes_per_thread, int parts);
 
-/* Autotuner: times every valid launch shape on subset 0 of the bound data (a uniform
- * image), keeps the fastest in the plan and returns it; also times the RDP stencil tile
+/* Autotuner: times every valid launch shape on four subsets spread over the views of the
+ * bound data (a uniform image), keeps the fastest in the plan and returns it; also times the RDP stencil tile
  * (32 x 8 voxels x 2, 4 or 8 slices per block) on the plan's image and keeps the fastest
  * for the plan's prior evaluations (solvers, pet_objective_grad).  Uses plan scratch;
  * synchronises `stream`.  Requires pet_plan_set_data. */

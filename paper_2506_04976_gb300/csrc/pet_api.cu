@@ -593,12 +593,13 @@ extern "C" pet_status pet_plan_autotune(pet_plan *plan, void *stream, int *plane
     return PET_ERR_CUDA;
   }
   const int old_k = plan->dp.grad_k, old_s = plan->dp.grad_split;
-  // Two rounds over every valid shape, 12 timed launches each after 2 untimed ones; a
-  // shape's time is its faster round (the best shapes differ by a few percent).
+  // Three rounds over every valid shape, 12 timed launches each (on four subsets in turn)
+  // after 2 untimed ones; a shape's time is its fastest round (the best shapes differ by a
+  // few percent).
   float tmin[3][5];
   for (auto &row : tmin)
     for (float &t : row) t = 1e30f;
-  for (int round = 0; round < 2; ++round)
+  for (int round = 0; round < 3; ++round)
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 5; ++b) {
       if (ks[a] > max_planes(plan->dp) || ss[b] > max_split(plan->dp)) continue;
@@ -608,7 +609,10 @@ extern "C" pet_status pet_plan_autotune(pet_plan *plan, void *stream, int *plane
       bool fail = false;
       for (int it = 0; it < 14 && !fail; ++it) {
         if (it == 2) fail |= cudaEventRecord(e0, st) != cudaSuccess;
-        fail |= launch_grad(plan->dp, 0, nullptr, x, plan->d_xT, g, plan->d_gT, nullptr, MODE_GRAD, nullptr, st) !=
+        // four subsets spread over the views (their view angles, hence driving axes and
+        // TOF directions, differ)
+        const int sub = ((it % 4) * plan->g.nsubsets) / 4;
+        fail |= launch_grad(plan->dp, sub, nullptr, x, plan->d_xT, g, plan->d_gT, nullptr, MODE_GRAD, nullptr, st) !=
                 cudaSuccess;
       }
       fail |= cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
