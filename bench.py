@@ -105,9 +105,12 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def source_hash():
+def source_hash(kernel_name):
+    """Hash of the sources a fused-gradient kernel is built from: the windowed TOF kernels
+    (tof_kernels.cu) or the others (proj_kernels.cu), with the shared header."""
+    files = ("tof_kernels.cu" if kernel_name.startswith("k_grad_tof") else "proj_kernels.cu", "pet_internal.cuh")
     h = hashlib.sha256()
-    for f in ("proj_kernels.cu", "tof_kernels.cu", "pet_internal.cuh"):
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_2506_04976_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -119,7 +122,7 @@ def ncu_instructions(kernel_tag, kernel_name):
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    if d.get("source_hash") != source_hash():
+    if d.get("source_hash") != source_hash(kernel_name):
         return None
     return d.get("warp_instructions_per_launch", {}).get(kernel_name)
 
@@ -132,7 +135,7 @@ def ncu_traffic(kernel_tag, kernel_name):
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    if d.get("source_hash") != source_hash():
+    if d.get("source_hash") != source_hash(kernel_name):
         return None
     return d.get("dram_bytes_per_launch", {}).get(kernel_name)
 
@@ -817,27 +820,51 @@ def measure_svrg(pet, dev, cfg, p, dt, args, rank, world, pg, e2e=True, clk=None
            "grads_per_step": grads_per_step, "shape": shape, "kernel_ms": kern_ms / max(kern_n, 1),
            "kernel_launches": kern_n, "T": T, "y_itemsize": dt["y"].element_size()}
     if e2e:
+        # Every step's counts and background are copied from pinned host memory; the copy of
+        # step i + 1 runs on a second stream into the other of two device buffer sets while
+        # step i computes, and pet_plan_set_counts binds each set before its step.
         y_host = torch.empty(dt["y"].shape, dtype=dt["y"].dtype, pin_memory=True)
         r_host = torch.empty(dt["r"].shape, dtype=dt["r"].dtype, pin_memory=True)
         y_host.copy_(dt["y"])
         r_host.copy_(dt["r"])
+        bufs = [(dt["y"], dt["r"]), (torch.empty_like(dt["y"]), torch.empty_like(dt["r"]))]
         x0_host = x0.cpu().pin_memory()
         x_dev = torch.empty_like(x0)
         xo = torch.empty(plan.img_shape, pin_memory=True)
+        main = torch.cuda.current_stream(dev)
+        cs = torch.cuda.Stream(device=dev)
+        copied = [torch.cuda.Event(), torch.cuda.Event()]
+        done = [torch.cuda.Event(), torch.cuda.Event()]
+        cp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+
+        def issue_copy(i):
+            j = i % 2
+            if i >= 2:
+                cs.wait_event(done[j])  # step i - 2 has finished with this buffer set
+            cp[i][0].record(cs)
+            with torch.cuda.stream(cs):
+                bufs[j][0].copy_(y_host, non_blocking=True)
+                bufs[j][1].copy_(r_host, non_blocking=True)
+            cp[i][1].record(cs)
+            copied[j].record(cs)
+
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        cp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        a.record()
+        a.record(main)
+        cs.wait_stream(main)
+        issue_copy(0)
         for i in range(args.steps):
-            cp[i][0].record()
-            dt["y"].copy_(y_host, non_blocking=True)
-            dt["r"].copy_(r_host, non_blocking=True)
+            j = i % 2
+            if i + 1 < args.steps:
+                issue_copy(i + 1)
+            main.wait_event(copied[j])
+            plan.set_counts(*bufs[j])
             x_dev.copy_(x0_host, non_blocking=True)
-            cp[i][1].record()
             solver.set_image(x_dev)
             solver.run(step_len)
+            done[j].record(main)
             xo.copy_(solver.image(), non_blocking=True)
-        b.record()
+        b.record(main)
         torch.cuda.synchronize()
         te = max_over_ranks(pg, a.elapsed_time(b) / 1e3, dev)
         h2d_ms = sum(c0.elapsed_time(c1) for c0, c1 in cp) / args.steps
@@ -845,7 +872,12 @@ def measure_svrg(pet, dev, cfg, p, dt, args, rank, world, pg, e2e=True, clk=None
                       "h2d_bytes_per_step": int(y_host.numel() * y_host.element_size() + r_host.numel() * 4 +
                                                 x0_host.numel() * 4),
                       "d2h_bytes_per_step": int(xo.numel() * 4), "ms_per_step": 1e3 * te / args.steps,
-                      "h2d_ms_per_step": h2d_ms}
+                      "h2d_ms_per_step": h2d_ms,
+                      "h2d_gbs": (y_host.numel() * y_host.element_size() + r_host.numel() * 4) / (h2d_ms * 1e6),
+                      "overlap": "counts and background of step i + 1 copied on a second stream during step i "
+                                 "(two device buffer sets bound by pet_plan_set_counts); the first copy is not hidden"}
+        plan.set_counts(dt["y"], dt["r"])
+        del bufs
         solver.kernel_time()
         del y_host, r_host
     del solver, plan

@@ -100,6 +100,24 @@ void pet_plan_destroy(pet_plan *plan);
 pet_status pet_plan_set_data(pet_plan *plan, const void *y, pet_ytype yt, const float *r,
                              const float *mu, const float *sens_lor, void *stream);
 
+/* Rebinds the counts and background only (borrowed, same layout and types as in
+ * pet_plan_set_data), keeping the multiplicative factors and sensitivity images: the
+ * next frame of a dynamic or gated acquisition on the same scanner and attenuation map
+ * (Sec. 1.1: m and A^T 1 depend on neither y nor r).  No device work; calls issued after
+ * it read the new arrays.  Solvers on the plan see them from their next iteration; their
+ * gradient tables (SAGA, SVRG) still hold gradients of the old data until
+ * pet_solver_set_image restarts them.  PET_ERR_STATE before pet_plan_set_data. */
+pet_status pet_plan_set_counts(pet_plan *plan, const void *y, pet_ytype yt, const float *r);
+
+/* Copies `bytes` from page-locked host memory (cudaHostAlloc / cudaHostRegister, or a
+ * pinned torch tensor) into device memory with a kernel whose threads load the host
+ * memory through the unified address space, 16 bytes at a time with several loads in
+ * flight (the ingest of a frame's counts and background before pet_plan_set_counts).
+ * Both pointers 16-byte aligned; src must be page-locked host memory and dst device
+ * memory of the current device, else PET_ERR_ARG.  Asynchronous on `stream`; the caller
+ * keeps src unchanged until the stream passes the copy. */
+pet_status pet_copy_to_device(void *dst, const void *src, size_t bytes, void *stream);
+
 /* Number of views of subset s (s = -1: all views). */
 pet_status pet_subset_size(const pet_plan *plan, int subset, int *nviews);
 

@@ -84,6 +84,8 @@ _sigs = {
     "pet_plan_create": (C.c_int, [C.POINTER(Geometry), C.POINTER(_vp)]),
     "pet_plan_destroy": (None, [_vp]),
     "pet_plan_set_data": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
+    "pet_plan_set_counts": (C.c_int, [_vp, _vp, C.c_int, _vp]),
+    "pet_copy_to_device": (C.c_int, [_vp, _vp, C.c_size_t, _vp]),
     "pet_subset_size": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int)]),
     "pet_plan_mult": (_vp, [_vp]),
     "pet_plan_sensitivity": (_vp, [_vp, C.c_int]),
@@ -207,6 +209,16 @@ class Plan:
                                    _stream()), "pet_plan_set_data")
         self._keep = [y, r]
 
+    def set_counts(self, y, r):
+        """Rebinds counts and background only (the next frame on the same scanner and
+        attenuation map): no device work, the factors and sensitivities are kept."""
+        if y.dtype not in _YT:
+            raise ValueError("y must be uint16, int32/uint32 or float32")
+        nbin = int(np.prod(self.sino_shape))
+        _ck(_lib.pet_plan_set_counts(self._h, _ptr(y, None, nbin), _YT[y.dtype], _ptr(r, numel=nbin)),
+            "pet_plan_set_counts")
+        self._keep = [y, r]
+
     def mult(self):
         p = _lib.pet_plan_mult(self._h)
         return _wrap(p, self.lor_shape)
@@ -290,6 +302,19 @@ class Plan:
 def launch_count():
     """Kernels launched by the library so far (graph replays count their kernel nodes)."""
     return _lib.pet_launch_count()
+
+
+def copy_to_device(dst, src):
+    """Kernel copy of a pinned host tensor into a CUDA tensor of the same dtype and size
+    (pet_copy_to_device) on the current stream."""
+    if not (dst.is_cuda and dst.is_contiguous()):
+        raise ValueError("dst: expected a contiguous CUDA tensor")
+    if src.is_cuda or not src.is_contiguous() or not src.is_pinned():
+        raise ValueError("src: expected a contiguous pinned host tensor")
+    if src.dtype != dst.dtype or src.numel() != dst.numel():
+        raise ValueError("src and dst differ in dtype or size")
+    _ck(_lib.pet_copy_to_device(_vp(dst.data_ptr()), _vp(src.data_ptr()), src.numel() * src.element_size(),
+                                _stream()), "pet_copy_to_device")
 
 
 def _wrap(ptr, shape):

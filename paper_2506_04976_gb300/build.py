@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpetgb300.so")
-SOURCES = ["proj_kernels.cu", "tof_kernels.cu", "image_kernels.cu", "solver.cu", "pet_api.cu", "pet_noalloc.cu"]
+SOURCES = ["proj_kernels.cu", "tof_kernels.cu", "image_kernels.cu", "solver.cu", "pet_api.cu", "pet_noalloc.cu", "ingest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -413,6 +413,15 @@ extern "C" pet_status pet_plan_set_data(pet_plan *plan, const void *y, pet_ytype
   return PET_OK;
 }
 
+extern "C" pet_status pet_plan_set_counts(pet_plan *plan, const void *y, pet_ytype yt, const float *r) {
+  if (!plan || !y || !r || (int)yt < 0 || (int)yt > 2) return PET_ERR_ARG;
+  if (!plan->has_data) return PET_ERR_STATE;
+  plan->dp.y = y;
+  plan->dp.yt = (int)yt;
+  plan->dp.r = r;
+  return PET_OK;
+}
+
 extern "C" pet_status pet_plan_check(pet_plan *plan, void *stream) {
   if (!plan) return PET_ERR_ARG;
   int h = 0;

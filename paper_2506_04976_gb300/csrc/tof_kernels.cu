@@ -55,6 +55,25 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
   return d;
 }
 
+// d = a * b and d = a - b on two lanes at once (mul.rn.f32x2, sub.rn.f32x2).
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
 template <int NT>
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double red[NT / 32];
@@ -187,21 +206,41 @@ __device__ __forceinline__ double tof_group(const DevPlan &P, const float4 *__re
       const int ib = min(max((int)fbf, -kTofPad), Nb);
       const float wb = fb - fbf;
       const int rowp = i * Nbp + ib + kTofPad;
-      float val[K];
-      bool any = false;
+      // bilinear interpolation: the two rows of each plane in one packed pair, then the
+      // axial step for two planes at a time
+      const float2 wbb = make_float2(wb, wb), wbb1 = make_float2(1.f - wb, 1.f - wb);
+      float2 h[K];
+      float wzk[K];
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const float fz = fmaf((float)i, dfz[k], fz0[k]);
         const float fzf = floorf(fz);
         const int iz = min(max((int)fzf, -kTofPad), P.nz);
-        const float wz = fz - fzf;
+        wzk[k] = fz - fzf;
         const int base = (iz + kTofPad) * planep + rowp;
         const float v00 = __ldg(imgp + base);
         const float v01 = __ldg(imgp + base + 1);
         const float v10 = __ldg(imgp + base + planep);
         const float v11 = __ldg(imgp + base + planep + 1);
-        const float v = (1.f - wz) * ((1.f - wb) * v00 + wb * v01) + wz * ((1.f - wb) * v10 + wb * v11);
-        val[k] = pv[k] ? v : 0.f;
+        h[k] = fma2(wbb, make_float2(v01, v11), mul2(wbb1, make_float2(v00, v10)));
+      }
+      float val[K];
+      if (K == 1) {
+        val[0] = fmaf(wzk[0], h[0].y, (1.f - wzk[0]) * h[0].x);
+      } else {
+#pragma unroll
+        for (int k = 0; k + 1 < K; k += 2) {
+          const float2 wz2 = make_float2(wzk[k], wzk[k + 1]);
+          const float2 r2 = fma2(wz2, make_float2(h[k].y, h[k + 1].y),
+                                 mul2(sub2(make_float2(1.f, 1.f), wz2), make_float2(h[k].x, h[k + 1].x)));
+          val[k] = r2.x;
+          val[k + 1] = r2.y;
+        }
+      }
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        val[k] = pv[k] ? val[k] : 0.f;
         any |= val[k] != 0.f;
       }
       if (!any) continue;
@@ -330,6 +369,7 @@ __device__ __forceinline__ double tof_group(const DevPlan &P, const float4 *__re
       const float wb = fb - fbf;
       if ((unsigned)(ib + 1) > (unsigned)Nb) continue;  // both in-plane neighbours outside
       const int rowp = i * Nbp + ib + kTofPad;
+      const float2 wbp = make_float2(1.f - wb, wb);
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         if (val[k] == 0.f) continue;
@@ -339,12 +379,14 @@ __device__ __forceinline__ double tof_group(const DevPlan &P, const float4 *__re
         const float wz = fz - fzf;
         if ((unsigned)(iz + 1) > (unsigned)P.nz) continue;  // both axial neighbours outside
         const int base = (iz + kTofPad) * planep + rowp;
-        const float a0 = (1.f - wz) * val[k], a1 = wz * val[k];
-        atomicAdd(outp + base, (1.f - wb) * a0);
-        atomicAdd(outp + base + 1, wb * a0);
+        const float2 a = mul2(make_float2(1.f - wz, wz), make_float2(val[k], val[k]));
+        const float2 lo2 = mul2(wbp, make_float2(a.x, a.x));
+        atomicAdd(outp + base, lo2.x);
+        atomicAdd(outp + base + 1, lo2.y);
         if (wz != 0.f) {  // the upper row of a plane through slice centres has weight 0
-          atomicAdd(outp + base + planep, (1.f - wb) * a1);
-          atomicAdd(outp + base + planep + 1, wb * a1);
+          const float2 up2 = mul2(wbp, make_float2(a.y, a.y));
+          atomicAdd(outp + base + planep, up2.x);
+          atomicAdd(outp + base + planep + 1, up2.y);
         }
       }
     }

@@ -352,6 +352,40 @@ def test_y_zero_and_zero_image():
     assert abs(float(obj) - ref) <= 1e-5 * ref
 
 
+@pytest.mark.parametrize("key", ["3d", "tof"])
+def test_set_counts_rebinds_counts_and_background(key):
+    """A second frame bound with set_counts gives the oracle's objective and gradient of
+    that frame's counts and background with the first frame's factors m (Sec. 1.1)."""
+    c = case(key)
+    rng = np.random.default_rng(7)
+    y2 = rng.poisson(1.5 * c.p["y"].astype(np.float64) + 0.2).astype(np.int32)
+    r2 = (0.7 * c.p["r"].astype(np.float64) + 0.01).astype(np.float32)
+    y2d, r2d = _y_tensor(y2), _t(r2)
+    try:
+        c.plan.set_counts(y2d, r2d)
+        s = 2
+        obj, g = c.plan.objective_grad(c.xt, s)
+        g = g.cpu().numpy()
+        val, gd = O.data_grad(c.G, c.n, s, c.x, c.m, r2, y2)
+        scale = O.sensitivity(c.G, c.n, s, c.m)
+        d = np.abs(g - gd)
+        assert np.linalg.norm(d) <= 1e-5 * np.linalg.norm(scale)
+        assert np.all(d <= 1e-4 * scale + 1e-6 * scale.max())
+        assert abs(float(obj) - val) <= 1e-5 * abs(val)
+        assert np.allclose(c.plan.sensitivity(s).cpu().numpy(), scale, rtol=1e-4, atol=1e-5 * scale.max())
+    finally:
+        c.plan.set_counts(c.y, c.r)
+
+
+def test_set_counts_needs_bound_data():
+    pet = _pet()
+    plan = pet.Plan(case("c1").g, 6)
+    y = torch.zeros(plan.sino_shape, device=DEV, dtype=torch.int32)
+    with pytest.raises(pet.PetError) as e:
+        plan.set_counts(y, torch.zeros(plan.sino_shape, device=DEV))
+    assert e.value.status == 7
+
+
 @pytest.mark.parametrize("key", ["c1", "3d", "tof", "tof13", "tof5", "tof25"])
 @pytest.mark.parametrize("shape", [(1, 1), (1, 2), (1, 4), (1, 8), (1, 16), (2, 1), (2, 2), (2, 4), (2, 8), (2, 16),
                                    (4, 1), (4, 2), (4, 4), (4, 8), (4, 16)])
