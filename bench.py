@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-copy", default="engine", choices=["engine", "kernel", "serial"],
+                    help="e2e ingest: the next step's data copied during the current step by the copy "
+                         "engines (engine) or by pet_copy_to_device (kernel), or copied by "
+                         "pet_copy_to_device before each step (serial)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-nrmse", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -291,6 +295,30 @@ def oracle_sampled_rate(p, subset=0, planes_every=1, workers=None):
     return {"value": 1.0 / t_grad, "unit": UNIT, "cores": timing["workers"], "kind": "oracle", "sample": sample}
 
 
+def oracle_subset_rate_mp(p, subset=0, workers=None):
+    """The FP64 oracle on one whole subset gradient of a host-generated workload, its data
+    term split over host processes by view and run of planes (oracle.pieces; the slowest
+    worker's compute time), plus one single-threaded RDP gradient."""
+    import oracle as O
+    from oracle import pieces
+    g = p["geom"]
+    workers = workers or oracle_workers()
+    views = [int(v) for v in O.subset_views(g["nview"], p["nsub"], subset)]
+    P = len(g["z1"])
+    chunk = max(1, -(-P * len(views) // (2 * workers)))
+    x = np.maximum(p["x_true"], 0.05 * p["x_true"].max()).astype(np.float32)
+    timing = {}
+    pieces.data_grad_subset(g, views, x, p["mu"].astype(np.float32), p["sens"][views], p["r"][views], p["y"][views],
+                            workers=workers, chunk=min(chunk, P), timing=timing)
+    t0 = time.perf_counter()
+    O.rdp(x.astype(np.float64), (g["dx"], g["dy"], g["dz"]), p["gamma"], p["eps"])
+    t_rdp = time.perf_counter() - t0
+    t = timing["seconds"] + t_rdp
+    return {"subset_grads_per_s": 1.0 / t, "cores": timing["workers"],
+            "sample": f"one subset gradient, FP64, data term over {timing['workers']} processes "
+                      f"({timing['seconds']:.3f} s, slowest worker) + single-threaded RDP ({t_rdp:.3f} s)"}
+
+
 def run_reference(args, rank, world):
     """The reference arm: the FP64 oracle as it stands on the host cores, on a bounded
     sample of the headline workload per step (rank 0 only)."""
@@ -459,6 +487,7 @@ def run_configs(args, pet, dev):
             times = cpu_baseline(p, 0, steps=1 if T > 1 else 2)
             r["cpu_oracle"] = {"subset_grads_per_s": len(times) / sum(times), "cores": 1,
                                "sample": f"{len(times)} subset gradient(s), FP64, 1 thread"}
+            r["cpu_oracle_processes"] = oracle_subset_rate_mp(p)
         out["configs"][cfg] = r
     print(json.dumps(out), flush=True)
 
@@ -820,44 +849,55 @@ def measure_svrg(pet, dev, cfg, p, dt, args, rank, world, pg, e2e=True, clk=None
            "grads_per_step": grads_per_step, "shape": shape, "kernel_ms": kern_ms / max(kern_n, 1),
            "kernel_launches": kern_n, "T": T, "y_itemsize": dt["y"].element_size()}
     if e2e:
-        # Every step's counts, background and start image are copied from pinned host memory
-        # by the library's ingest kernel (pet_copy_to_device: SM loads over the CPU-GPU link,
-        # no copy engine); the copy of step i + 1 runs on a second stream into the other of
-        # two device buffer sets while step i computes, and pet_plan_set_counts binds each
-        # set before its step.
+        # Every step's counts, background and start image are copied from pinned host memory.
+        # engine / kernel: the copy of step i + 1 runs on a second stream (copy engines, or the
+        # library's ingest kernel pet_copy_to_device) into the other of two device buffer
+        # sets while step i computes, and pet_plan_set_counts binds each set before its step;
+        # serial: pet_copy_to_device into the plan's buffers before each step.  The start
+        # image always goes through pet_copy_to_device on the step's stream.
+        how = getattr(args, "e2e_copy", "engine")
         y_host = torch.empty(dt["y"].shape, dtype=dt["y"].dtype, pin_memory=True)
         r_host = torch.empty(dt["r"].shape, dtype=dt["r"].dtype, pin_memory=True)
         y_host.copy_(dt["y"])
         r_host.copy_(dt["r"])
-        bufs = [(dt["y"], dt["r"]), (torch.empty_like(dt["y"]), torch.empty_like(dt["r"]))]
         x0_host = x0.cpu().pin_memory()
         x_dev = torch.empty_like(x0)
         xo = torch.empty(plan.img_shape, pin_memory=True)
         main = torch.cuda.current_stream(dev)
-        cs = torch.cuda.Stream(device=dev)
+        serial = how == "serial"
+        cs = main if serial else torch.cuda.Stream(device=dev)
+        bufs = [(dt["y"], dt["r"])] * 2 if serial else \
+            [(dt["y"], dt["r"]), (torch.empty_like(dt["y"]), torch.empty_like(dt["r"]))]
         copied = [torch.cuda.Event(), torch.cuda.Event()]
         done = [torch.cuda.Event(), torch.cuda.Event()]
         cp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
 
         def issue_copy(i):
             j = i % 2
-            if i >= 2:
+            if i >= 2 and not serial:
                 cs.wait_event(done[j])  # step i - 2 has finished with this buffer set
             cp[i][0].record(cs)
             with torch.cuda.stream(cs):
-                pet.copy_to_device(bufs[j][0], y_host)
-                pet.copy_to_device(bufs[j][1], r_host)
+                if how == "engine":
+                    bufs[j][0].copy_(y_host, non_blocking=True)
+                    bufs[j][1].copy_(r_host, non_blocking=True)
+                else:
+                    pet.copy_to_device(bufs[j][0], y_host)
+                    pet.copy_to_device(bufs[j][1], r_host)
             cp[i][1].record(cs)
             copied[j].record(cs)
 
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(main)
-        cs.wait_stream(main)
-        issue_copy(0)
+        if not serial:
+            cs.wait_stream(main)
+            issue_copy(0)
         for i in range(args.steps):
             j = i % 2
-            if i + 1 < args.steps:
+            if serial:
+                issue_copy(i)
+            elif i + 1 < args.steps:
                 issue_copy(i + 1)
             main.wait_event(copied[j])
             plan.set_counts(*bufs[j])
@@ -876,9 +916,13 @@ def measure_svrg(pet, dev, cfg, p, dt, args, rank, world, pg, e2e=True, clk=None
                       "d2h_bytes_per_step": int(xo.numel() * 4), "ms_per_step": 1e3 * te / args.steps,
                       "h2d_ms_per_step": h2d_ms,
                       "h2d_gbs": (y_host.numel() * y_host.element_size() + r_host.numel() * 4) / (h2d_ms * 1e6),
-                      "overlap": "counts and background of step i + 1 copied by pet_copy_to_device on a second "
-                                 "stream during step i (two device buffer sets bound by pet_plan_set_counts; "
-                                 "the copy kernel shares the SMs with the step); the first copy is not hidden"}
+                      "ingest": {"engine": "counts and background of step i + 1 copied by the copy engines on a "
+                                           "second stream during step i (two device buffer sets bound by "
+                                           "pet_plan_set_counts; the first copy is not hidden), start image by "
+                                           "pet_copy_to_device",
+                                 "kernel": "as engine, with pet_copy_to_device (the copy kernel shares the SMs "
+                                           "with the step)",
+                                 "serial": "pet_copy_to_device before each step"}[how]}
         plan.set_counts(dt["y"], dt["r"])
         del bufs
         solver.kernel_time()

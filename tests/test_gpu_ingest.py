@@ -58,3 +58,40 @@ def test_second_frame_through_ingest_and_set_counts():
     assert np.linalg.norm(d) <= 1e-5 * np.linalg.norm(scale)
     assert np.all(d <= 1e-4 * scale + 1e-6 * scale.max())
     assert abs(float(obj) - val) <= 1e-5 * abs(val)
+
+
+def test_solver_follows_set_counts_between_runs():
+    """A solver restarted after pet_plan_set_counts reconstructs the new frame: its graph-
+    replayed SVRG epochs equal those of a solver on a plan bound to that frame from the
+    start (same launch shape and subset order; only the atomics' order differs)."""
+    from paper_2506_04976_gb300 import binding as pet, synth
+    p = synth.make_problem("c2", 0, nx=40, nz=23, nrad=70, nview=36, nsub=6)
+    mu = torch.from_numpy(p["mu"].astype(np.float32)).to(DEV)
+    sens = torch.from_numpy(p["sens"].astype(np.float32)).to(DEV)
+    y1 = torch.from_numpy(p["y"].astype(np.int32)).to(DEV)
+    r1 = torch.from_numpy(p["r"]).to(DEV)
+    rng = np.random.default_rng(11)
+    y2 = torch.from_numpy(rng.poisson(1.7 * p["y"].astype(np.float64) + 0.1).astype(np.int32)).to(DEV)
+    r2 = torch.from_numpy((0.8 * p["r"].astype(np.float64)).astype(np.float32)).to(DEV)
+    x0 = torch.full(tuple(p["x_true"].shape), float(p["x_true"].mean()), device=DEV)
+    kw = dict(algo=pet.SVRG, step_rule=pet.STEP_VANISH, tau0=1.0, eta=0.02, precond_kind=1, pc_iters=(0, 6),
+              beta=p["beta"], gamma=p["gamma"], eps=p["eps"], seed=5, use_graph=True)
+    a = pet.Plan(p["geom"], 6)
+    a.set_data(y1, r1, mu, sens)
+    a.set_grad_shape(2, 1)
+    sa = pet.Solver(a, **kw)
+    sa.set_image(x0)
+    sa.run(18)
+    a.set_counts(y2, r2)
+    sa.set_image(x0)
+    sa.run(24)
+    b = pet.Plan(p["geom"], 6)
+    b.set_data(y2, r2, mu, sens)
+    b.set_grad_shape(2, 1)
+    sb = pet.Solver(b, **kw)
+    sb.set_image(x0)
+    sb.run(24)
+    torch.cuda.synchronize()
+    xa, xb = sa.image().cpu().numpy().astype(np.float64), sb.image().cpu().numpy().astype(np.float64)
+    assert np.array_equal(sa.subsets(), sb.subsets())
+    assert np.linalg.norm(xa - xb) <= 1e-5 * np.linalg.norm(xb)
