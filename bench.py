@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--workload", default="c5", choices=["c5", "c2"],
                     help="step mode: the workload of the headline line (the other one is added as a key)")
     ap.add_argument("--no-c2", action="store_true", help="step mode: skip the secondary c2 measurement")
-    ap.add_argument("--study-config", default="c1", choices=["c1", "c1b5", "c1b50", "c2", "c2s", "c2s1", "c2s16", "c3s"],
+    ap.add_argument("--study-config", default="c1", choices=["c1", "c1b5", "c1b50", "c2", "c2s", "c2s1", "c2s16", "c2sb50", "c3s"],
                     help="study mode: workload with a converged reference image in tests/golden")
     ap.add_argument("--study-nsub", type=int, default=0,
                     help="study mode: number of subsets (0: the workload's own; Sec. 3.2 uses 27)")

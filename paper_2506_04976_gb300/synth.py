@@ -338,13 +338,14 @@ def _smooth(a, sigma):
 # resolution in every direction: 64x64x23 voxels of 4x4x5.7 mm, 125 radial bins x 84
 # views, 21 subsets of 4 views), with the relative prior strength 4 ("c2s"), 1 or 16,
 # and the TOF workload c3 (11 bins, 1e6 counts) at the same half resolution ("c3s"); the
-# 2D workload with priors 50 and 500 times stronger than its own ("c1b5", "c1b50"), where
-# the prior's curvature term of the harmonic preconditioner (eq. 8) reaches ~10% and ~100%
-# of the sensitivity A^T 1.
+# 2D workload with priors 50 and 500 times stronger than its own ("c1b5", "c1b50") and the
+# half-resolution 3D one with beta = 50 ("c2sb50"), where the prior's curvature term of the
+# harmonic preconditioner (eq. 8) reaches ~10% and ~100% of the sensitivity A^T 1.
 STUDY_WORKLOADS = {"c2s": dict(nx=64, nz=23, nrad=125, nview=84, nsub=21),
                    "c2s1": dict(nx=64, nz=23, nrad=125, nview=84, nsub=21, beta=1 * 2e-4 * 1e7 / 3e7),
                    "c2s16": dict(nx=64, nz=23, nrad=125, nview=84, nsub=21, beta=16 * 2e-4 * 1e7 / 3e7),
                    "c3s": dict(base="c3", nx=64, nz=23, nrad=125, nview=84, nsub=21),
+                   "c2sb50": dict(nx=64, nz=23, nrad=125, nview=84, nsub=21, beta=50.0),
                    "c1b5": dict(base="c1", beta=5.0),
                    "c1b50": dict(base="c1", beta=50.0)}
 
