@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-copy-blocks", type=int, default=8,
+                    help="e2e ingest kernel: grid bound of pet_copy_to_device (0: four blocks per SM; 8 "
+                         "blocks already move 175 GB/s)")
     ap.add_argument("--e2e-copy", default="engine", choices=["engine", "kernel", "serial"],
                     help="e2e ingest: the next step's data copied during the current step by the copy "
                          "engines (engine) or by pet_copy_to_device (kernel), or copied by "
@@ -849,13 +852,15 @@ def measure_svrg(pet, dev, cfg, p, dt, args, rank, world, pg, e2e=True, clk=None
            "grads_per_step": grads_per_step, "shape": shape, "kernel_ms": kern_ms / max(kern_n, 1),
            "kernel_launches": kern_n, "T": T, "y_itemsize": dt["y"].element_size()}
     if e2e:
-        # Every step's counts, background and start image are copied from pinned host memory.
-        # engine / kernel: the copy of step i + 1 runs on a second stream (copy engines, or the
-        # library's ingest kernel pet_copy_to_device) into the other of two device buffer
-        # sets while step i computes, and pet_plan_set_counts binds each set before its step;
-        # serial: pet_copy_to_device into the plan's buffers before each step.  The start
-        # image always goes through pet_copy_to_device on the step's stream.
+        # The same SVRG outer loops as above, one reconstruction started from the pinned host
+        # copy of the start image, with every step's counts and background copied from pinned
+        # host memory and the image read back after every step.  engine / kernel: the copy
+        # of step i + 1 runs on a second stream (the copy engines, or the library's ingest
+        # kernel pet_copy_to_device on a few SMs) into the other of two device buffer sets
+        # while step i computes, and pet_plan_set_counts binds each set before its step;
+        # serial: pet_copy_to_device into the plan's buffers before each step.
         how = getattr(args, "e2e_copy", "engine")
+        cblocks = getattr(args, "e2e_copy_blocks", 8)
         y_host = torch.empty(dt["y"].shape, dtype=dt["y"].dtype, pin_memory=True)
         r_host = torch.empty(dt["r"].shape, dtype=dt["r"].dtype, pin_memory=True)
         y_host.copy_(dt["y"])
@@ -882,8 +887,8 @@ def measure_svrg(pet, dev, cfg, p, dt, args, rank, world, pg, e2e=True, clk=None
                     bufs[j][0].copy_(y_host, non_blocking=True)
                     bufs[j][1].copy_(r_host, non_blocking=True)
                 else:
-                    pet.copy_to_device(bufs[j][0], y_host)
-                    pet.copy_to_device(bufs[j][1], r_host)
+                    pet.copy_to_device(bufs[j][0], y_host, cblocks)
+                    pet.copy_to_device(bufs[j][1], r_host, cblocks)
             cp[i][1].record(cs)
             copied[j].record(cs)
 
@@ -901,8 +906,9 @@ def measure_svrg(pet, dev, cfg, p, dt, args, rank, world, pg, e2e=True, clk=None
                 issue_copy(i + 1)
             main.wait_event(copied[j])
             plan.set_counts(*bufs[j])
-            pet.copy_to_device(x_dev, x0_host)
-            solver.set_image(x_dev)
+            if i == 0:
+                pet.copy_to_device(x_dev, x0_host)
+                solver.set_image(x_dev)
             solver.run(step_len)
             done[j].record(main)
             xo.copy_(solver.image(), non_blocking=True)
@@ -912,16 +918,16 @@ def measure_svrg(pet, dev, cfg, p, dt, args, rank, world, pg, e2e=True, clk=None
         h2d_ms = sum(c0.elapsed_time(c1) for c0, c1 in cp) / args.steps
         out["e2e"] = {"value": whole_job_rate(grads_per_step * args.steps, world, te), "unit": UNIT,
                       "h2d_bytes_per_step": int(y_host.numel() * y_host.element_size() + r_host.numel() * 4 +
-                                                x0_host.numel() * 4),
+                                                x0_host.numel() * 4 / args.steps),
                       "d2h_bytes_per_step": int(xo.numel() * 4), "ms_per_step": 1e3 * te / args.steps,
                       "h2d_ms_per_step": h2d_ms,
                       "h2d_gbs": (y_host.numel() * y_host.element_size() + r_host.numel() * 4) / (h2d_ms * 1e6),
                       "ingest": {"engine": "counts and background of step i + 1 copied by the copy engines on a "
                                            "second stream during step i (two device buffer sets bound by "
-                                           "pet_plan_set_counts; the first copy is not hidden), start image by "
-                                           "pet_copy_to_device",
+                                           "pet_plan_set_counts; the first copy is not hidden); the start image "
+                                           "copied by pet_copy_to_device before the first step",
                                  "kernel": "as engine, with pet_copy_to_device (the copy kernel shares the SMs "
-                                           "with the step)",
+                                           f"with the step; grid bound {cblocks or 'four blocks per SM'})",
                                  "serial": "pet_copy_to_device before each step"}[how]}
         plan.set_counts(dt["y"], dt["r"])
         del bufs

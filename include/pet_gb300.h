@@ -113,10 +113,12 @@ pet_status pet_plan_set_counts(pet_plan *plan, const void *y, pet_ytype yt, cons
  * pinned torch tensor) into device memory with a kernel whose threads load the host
  * memory through the unified address space, 16 bytes at a time with several loads in
  * flight (the ingest of a frame's counts and background before pet_plan_set_counts).
- * Both pointers 16-byte aligned; src must be page-locked host memory and dst device
- * memory of the current device, else PET_ERR_ARG.  Asynchronous on `stream`; the caller
- * keeps src unchanged until the stream passes the copy. */
-pet_status pet_copy_to_device(void *dst, const void *src, size_t bytes, void *stream);
+ * max_blocks bounds the grid (blocks of 512 threads; 0 = four per SM): a few blocks keep
+ * most SMs free for kernels running beside the copy on another stream.  Both pointers
+ * 16-byte aligned; src must be page-locked host memory and dst device memory of the
+ * current device, max_blocks >= 0, else PET_ERR_ARG.  Asynchronous on `stream`; the
+ * caller keeps src unchanged until the stream passes the copy. */
+pet_status pet_copy_to_device(void *dst, const void *src, size_t bytes, int max_blocks, void *stream);
 
 /* Number of views of subset s (s = -1: all views). */
 pet_status pet_subset_size(const pet_plan *plan, int subset, int *nviews);

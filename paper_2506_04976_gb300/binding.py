@@ -85,7 +85,7 @@ _sigs = {
     "pet_plan_destroy": (None, [_vp]),
     "pet_plan_set_data": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
     "pet_plan_set_counts": (C.c_int, [_vp, _vp, C.c_int, _vp]),
-    "pet_copy_to_device": (C.c_int, [_vp, _vp, C.c_size_t, _vp]),
+    "pet_copy_to_device": (C.c_int, [_vp, _vp, C.c_size_t, C.c_int, _vp]),
     "pet_subset_size": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int)]),
     "pet_plan_mult": (_vp, [_vp]),
     "pet_plan_sensitivity": (_vp, [_vp, C.c_int]),
@@ -304,9 +304,10 @@ def launch_count():
     return _lib.pet_launch_count()
 
 
-def copy_to_device(dst, src):
+def copy_to_device(dst, src, max_blocks=0):
     """Kernel copy of a pinned host tensor into a CUDA tensor of the same dtype and size
-    (pet_copy_to_device) on the current stream."""
+    (pet_copy_to_device) on the current stream; max_blocks bounds its grid (0: four
+    blocks per SM)."""
     if not (dst.is_cuda and dst.is_contiguous()):
         raise ValueError("dst: expected a contiguous CUDA tensor")
     if src.is_cuda or not src.is_contiguous() or not src.is_pinned():
@@ -314,7 +315,7 @@ def copy_to_device(dst, src):
     if src.dtype != dst.dtype or src.numel() != dst.numel():
         raise ValueError("src and dst differ in dtype or size")
     _ck(_lib.pet_copy_to_device(_vp(dst.data_ptr()), _vp(src.data_ptr()), src.numel() * src.element_size(),
-                                _stream()), "pet_copy_to_device")
+                                int(max_blocks), _stream()), "pet_copy_to_device")
 
 
 def _wrap(ptr, shape):

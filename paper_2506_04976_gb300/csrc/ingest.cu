@@ -1,6 +1,9 @@
 // Host-to-device ingest of measured data with a kernel: SM loads of page-locked host
 // memory through the unified address space (over the CPU-GPU link), 16-byte vectors,
-// four loads in flight per thread, stored coalesced into device memory.
+// four loads in flight per thread, stored coalesced into device memory.  Loads and stores
+// carry the streaming cache hint (evict first): the data are touched once here and not
+// again until a later kernel, so they should not push a concurrently running kernel's
+// working set out of L2.
 #include <algorithm>
 
 #include "pet_internal.cuh"
@@ -14,13 +17,14 @@ __global__ void __launch_bounds__(512) k_copy_pinned(const uint4 *__restrict__ s
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (; i + 3 * stride < n; i += 4 * stride) {
-    const uint4 a = src[i], b = src[i + stride], c = src[i + 2 * stride], d = src[i + 3 * stride];
-    dst[i] = a;
-    dst[i + stride] = b;
-    dst[i + 2 * stride] = c;
-    dst[i + 3 * stride] = d;
+    const uint4 a = __ldcs(src + i), b = __ldcs(src + i + stride), c = __ldcs(src + i + 2 * stride),
+                d = __ldcs(src + i + 3 * stride);
+    __stcs(dst + i, a);
+    __stcs(dst + i + stride, b);
+    __stcs(dst + i + 2 * stride, c);
+    __stcs(dst + i + 3 * stride, d);
   }
-  for (; i < n; i += stride) dst[i] = src[i];
+  for (; i < n; i += stride) __stcs(dst + i, __ldcs(src + i));
 }
 
 __global__ void k_copy_tail(const unsigned char *__restrict__ src, unsigned char *__restrict__ dst, int n) {
@@ -33,8 +37,8 @@ __global__ void k_copy_tail(const unsigned char *__restrict__ src, unsigned char
 
 using namespace petgb;
 
-extern "C" pet_status pet_copy_to_device(void *dst, const void *src, size_t bytes, void *stream) {
-  if (!dst || !src) return PET_ERR_ARG;
+extern "C" pet_status pet_copy_to_device(void *dst, const void *src, size_t bytes, int max_blocks, void *stream) {
+  if (!dst || !src || max_blocks < 0) return PET_ERR_ARG;
   if (bytes == 0) return PET_OK;
   if (((uintptr_t)dst & 15) || ((uintptr_t)src & 15)) return PET_ERR_ARG;
   cudaPointerAttributes as{}, ad{};
@@ -53,7 +57,8 @@ extern "C" pet_status pet_copy_to_device(void *dst, const void *src, size_t byte
   unsigned char *d = static_cast<unsigned char *>(dst);
   if (n16) {
     const size_t want = (n16 + 511) / 512;
-    const int grid = (int)std::min<size_t>(want, (size_t)4 * nsm);
+    const size_t cap = max_blocks > 0 ? (size_t)max_blocks : (size_t)4 * nsm;
+    const int grid = (int)std::min<size_t>(want, cap);
     k_copy_pinned<<<grid, 512, 0, st>>>(reinterpret_cast<const uint4 *>(s), reinterpret_cast<uint4 *>(d), n16);
     note_launch();
   }

@@ -10,12 +10,13 @@ DEV = "cuda:0"
 
 
 @pytest.mark.parametrize("nbytes", [16, 17, 4096 + 5, 1_000_003, (3 << 20) + 48])
-def test_copy_to_device_is_bit_exact(nbytes):
+@pytest.mark.parametrize("max_blocks", [0, 1, 3])
+def test_copy_to_device_is_bit_exact(nbytes, max_blocks):
     from paper_2506_04976_gb300 import binding as pet
     rng = np.random.default_rng(nbytes)
     host = torch.from_numpy(rng.integers(0, 256, nbytes, dtype=np.uint8)).pin_memory()
     dev = torch.zeros(nbytes, dtype=torch.uint8, device=DEV)
-    pet.copy_to_device(dev, host)
+    pet.copy_to_device(dev, host, max_blocks)
     torch.cuda.synchronize()
     assert torch.equal(dev.cpu(), host)
 
@@ -28,6 +29,9 @@ def test_copy_to_device_rejects_bad_sources():
     host = torch.zeros(80, dtype=torch.uint8).pin_memory()
     with pytest.raises(pet.PetError) as e:
         pet.copy_to_device(dev, host[1:65])  # 1 byte past a 16-byte boundary
+    assert e.value.status == 1
+    with pytest.raises(pet.PetError) as e:
+        pet.copy_to_device(dev, host[:64], -1)
     assert e.value.status == 1
 
 
