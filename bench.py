@@ -114,8 +114,9 @@ def measured_peaks():
 
 def source_hash(kernel_name):
     """Hash of the sources a fused-gradient kernel is built from: the windowed TOF kernels
-    (tof_kernels.cu) or the others (proj_kernels.cu), with the shared header."""
-    files = ("tof_kernels.cu" if kernel_name.startswith("k_grad_tof") else "proj_kernels.cu", "pet_internal.cuh")
+    (tof_kernels.cu) or the others (proj_kernels.cu), with the shared headers."""
+    files = ("tof_kernels.cu" if kernel_name.startswith("k_grad_tof") else "proj_kernels.cu", "pet_internal.cuh",
+             "packed_f32x2.cuh")
     h = hashlib.sha256()
     for f in files:
         h.update(open(os.path.join(ROOT, "paper_2506_04976_gb300", "csrc", f), "rb").read())

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <atomic>
 
+#include "packed_f32x2.cuh"
 #include "pet_internal.cuh"
 
 namespace petgb {
@@ -361,6 +362,11 @@ __device__ __forceinline__ void grad_mp_body(const DevPlan &P, int subset, int b
       const bool b0 = (unsigned)ib < (unsigned)Nb;
       const bool b1 = (unsigned)(ib + 1) < (unsigned)Nb && wb != 0.f;
       const int row = i * Nb + ib;
+      // bilinear interpolation: the two rows of each plane as one packed pair, then the
+      // axial step for two planes at a time
+      const float2 wbb = make_float2(wb, wb), wbb1 = make_float2(1.f - wb, 1.f - wb);
+      float2 h[K];
+      float wzk[K];
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const float fz = fmaf((float)i, dfz[k], fz0[k]);
@@ -374,8 +380,20 @@ __device__ __forceinline__ void grad_mp_body(const DevPlan &P, int subset, int b
         const float v01 = (z0 && b1) ? __ldg(img + base + 1) : 0.f;
         const float v10 = (z1 && b0) ? __ldg(img + base + plane) : 0.f;
         const float v11 = (z1 && b1) ? __ldg(img + base + plane + 1) : 0.f;
-        const float val = (1.f - wz) * ((1.f - wb) * v00 + wb * v01) + wz * ((1.f - wb) * v10 + wb * v11);
-        kahan_add(acc[k], cmp[k], val);
+        h[k] = fma2(wbb, make_float2(v01, v11), mul2(wbb1, make_float2(v00, v10)));
+        wzk[k] = wz;
+      }
+      if (K == 1) {
+        kahan_add(acc[0], cmp[0], fmaf(wzk[0], h[0].y, (1.f - wzk[0]) * h[0].x));
+      } else {
+#pragma unroll
+        for (int k = 0; k + 1 < K; k += 2) {
+          const float2 wz2 = make_float2(wzk[k], wzk[k + 1]);
+          const float2 r2 = fma2(wz2, make_float2(h[k].y, h[k + 1].y),
+                                 mul2(sub2(make_float2(1.f, 1.f), wz2), make_float2(h[k].x, h[k + 1].x)));
+          kahan_add(acc[k], cmp[k], r2.x);
+          kahan_add(acc[k + 1], cmp[k + 1], r2.y);
+        }
       }
     }
     if (SPLIT > 1) {
@@ -433,6 +451,7 @@ __device__ __forceinline__ void grad_mp_body(const DevPlan &P, int subset, int b
       const bool b0 = (unsigned)ib < (unsigned)Nb;
       const bool b1 = (unsigned)(ib + 1) < (unsigned)Nb && wb != 0.f;
       const int row = i * Nb + ib;
+      const float2 wbp = make_float2(1.f - wb, wb);
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         if (q[k] == 0.f) continue;
@@ -443,11 +462,13 @@ __device__ __forceinline__ void grad_mp_body(const DevPlan &P, int subset, int b
         const bool z0 = (unsigned)iz < (unsigned)P.nz;
         const bool z1 = (unsigned)(iz + 1) < (unsigned)P.nz && wz != 0.f;
         const int base = iz * plane + row;
-        const float a0 = (1.f - wz) * q[k], a1 = wz * q[k];
-        if (z0 && b0) atomicAdd(out + base, (1.f - wb) * a0);
-        if (z0 && b1) atomicAdd(out + base + 1, wb * a0);
-        if (z1 && b0) atomicAdd(out + base + plane, (1.f - wb) * a1);
-        if (z1 && b1) atomicAdd(out + base + plane + 1, wb * a1);
+        const float2 a = mul2(make_float2(1.f - wz, wz), make_float2(q[k], q[k]));
+        const float2 lo2 = mul2(wbp, make_float2(a.x, a.x));
+        const float2 up2 = mul2(wbp, make_float2(a.y, a.y));
+        if (z0 && b0) atomicAdd(out + base, lo2.x);
+        if (z0 && b1) atomicAdd(out + base + 1, lo2.y);
+        if (z1 && b0) atomicAdd(out + base + plane, up2.x);
+        if (z1 && b1) atomicAdd(out + base + plane + 1, up2.y);
       }
     }
   }
