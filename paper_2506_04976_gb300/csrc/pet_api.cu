@@ -145,6 +145,19 @@ static pet_status build_tof_window(pet_plan *pl, const std::vector<float4> &plan
     return grp;
   };
   const std::vector<int> grp2 = groups(2), grp4 = groups(4);
+  // whether the planes of every group lie a whole number of slices apart (their axial
+  // positions then share one fraction along the LOR)
+  auto zs = [&](int p) { return (g.z1[p] + g.z2[p]) / (2.0 * g.dz); };
+  auto whole = [&](const std::vector<int> &grp, int K) {
+    for (size_t q = 0; q < grp.size(); q += K)
+      for (int k = 1; k < K; ++k) {
+        if (grp[q + k] < 0) continue;
+        const double d = zs(grp[q + k]) - zs(grp[q]);
+        if (fabs(d - nearbyint(d)) > 1e-9) return false;
+      }
+    return true;
+  };
+  dp.tof_zint = whole(grp2, 2) && whole(grp4, 4) ? 1 : 0;
   if (dalloc(&pl->d_tofw_tab, tab.size()) != cudaSuccess || dalloc(&pl->d_tof_grp2, grp2.size()) != cudaSuccess ||
       dalloc(&pl->d_tof_grp4, grp4.size()) != cudaSuccess || dalloc(&pl->d_tof_work, 1) != cudaSuccess)
     return PET_ERR_NOMEM;

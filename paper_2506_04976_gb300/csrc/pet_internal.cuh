@@ -57,6 +57,7 @@ struct DevPlan {
   int tof_ngrp2;
   const int *tof_grp4;     // [tof_ngrp4][4] plane quadruples of equal axial slope (-1: none)
   int tof_ngrp4;
+  int tof_zint;             // 1: the planes of every group lie a whole number of slices apart
   unsigned long long *tof_work;  // work counter of the persistent TOF kernel (plan scratch)
   int nsm;                       // multiprocessors of the plan's device
   float *tof_xp, *tof_xtp;       // zero-padded image copies in the two view frames (plan scratch)

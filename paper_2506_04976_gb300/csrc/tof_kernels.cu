@@ -101,7 +101,10 @@ __device__ __forceinline__ void win_weights(const float4 *__restrict__ tab, int 
 // the block's bin array (column tid of each row belongs to this thread; with SPLIT > 1 the
 // parts of LOR group tl exchange sums through columns j LPB + tl, so every thread of the
 // block must call this together).  The caller has cleared this thread's column.
-template <int K, int WIN, int SPLIT, int NT>
+// ZI: the planes of every group lie a whole number of slices apart (checked on the host),
+// so they share the fraction of their axial position along the LOR: plane k samples row
+// floor(z_0) + dz_k with the weight of plane 0, one floor per sample instead of K.
+template <int K, int WIN, int SPLIT, int NT, bool ZI = false>
 __device__ __forceinline__ double tof_group(const DevPlan &P, const float4 *__restrict__ s_tab, float *s_acc,
                                             int v, int r, int grp, bool ok, int part, int tl, int tid,
                                             const float *__restrict__ x, const float *__restrict__ xT,
@@ -120,6 +123,8 @@ __device__ __forceinline__ double tof_group(const DevPlan &P, const float4 *__re
   int pk[K];
   bool pv[K];
   float fz0[K], dfz[K];
+  int dzk[K];  // ZI: slice offset of plane k from plane 0
+  float zs0 = 0.f;
   float sec = 1.f;
   float lo_b = 0.f, hi_b = (float)(Na - 1);
   clip_range(fb0, dfb, -1.f, (float)Nb, lo_b, hi_b);
@@ -135,7 +140,9 @@ __device__ __forceinline__ double tof_group(const DevPlan &P, const float4 *__re
     if (k == 0) {  // planes of a group share their axial slope, hence sec and t
       const float kk = pl.z * inv2h;
       sec = sqrtf(fmaf(kk, kk, 1.f));
+      zs0 = pl.x;
     }
+    dzk[k] = k == 0 ? 0 : __float2int_rn(pl.x - zs0);
     float lk = lo_b, hk = hi_b;
     clip_range(fz0[k], dfz[k], -1.f, (float)P.nz, lk, hk);
     if (pv[k] && lk <= hk) { lo = fminf(lo, lk); hi = fmaxf(hi, hk); }
@@ -182,12 +189,27 @@ __device__ __forceinline__ double tof_group(const DevPlan &P, const float4 *__re
       const float2 wbb = make_float2(wb, wb), wbb1 = make_float2(1.f - wb, 1.f - wb);
       float2 h[K];
       float wzk[K];
+      int iz0 = 0;
+      float wz0 = 0.f;
+      if (ZI) {
+        const float fz = fmaf((float)i, dfz[0], fz0[0]);
+        const float fzf = floorf(fz);
+        iz0 = (int)fzf;
+        wz0 = fz - fzf;
+      }
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const float fz = fmaf((float)i, dfz[k], fz0[k]);
-        const float fzf = floorf(fz);
-        const int iz = min(max((int)fzf, -kTofPad), P.nz);
-        wzk[k] = fz - fzf;
+        int izk;
+        if (ZI) {
+          izk = iz0 + dzk[k];
+          wzk[k] = wz0;
+        } else {
+          const float fz = fmaf((float)i, dfz[k], fz0[k]);
+          const float fzf = floorf(fz);
+          izk = (int)fzf;
+          wzk[k] = fz - fzf;
+        }
+        const int iz = min(max(izk, -kTofPad), P.nz);
         const int base = (iz + kTofPad) * planep + rowp;
         const float v00 = __ldg(imgp + base);
         const float v01 = __ldg(imgp + base + 1);
@@ -341,13 +363,28 @@ __device__ __forceinline__ double tof_group(const DevPlan &P, const float4 *__re
       if ((unsigned)(ib + 1) > (unsigned)Nb) continue;  // both in-plane neighbours outside
       const int rowp = i * Nbp + ib + kTofPad;
       const float2 wbp = make_float2(1.f - wb, wb);
+      int iz0 = 0;
+      float wz0 = 0.f;
+      if (ZI) {
+        const float fz = fmaf((float)i, dfz[0], fz0[0]);
+        const float fzf = floorf(fz);
+        iz0 = (int)fzf;
+        wz0 = fz - fzf;
+      }
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         if (val[k] == 0.f) continue;
-        const float fz = fmaf((float)i, dfz[k], fz0[k]);
-        const float fzf = floorf(fz);
-        const int iz = (int)fzf;
-        const float wz = fz - fzf;
+        int iz;
+        float wz;
+        if (ZI) {
+          iz = iz0 + dzk[k];
+          wz = wz0;
+        } else {
+          const float fz = fmaf((float)i, dfz[k], fz0[k]);
+          const float fzf = floorf(fz);
+          iz = (int)fzf;
+          wz = fz - fzf;
+        }
         if ((unsigned)(iz + 1) > (unsigned)P.nz) continue;  // both axial neighbours outside
         const int base = (iz + kTofPad) * planep + rowp;
         const float2 a = mul2(make_float2(1.f - wz, wz), make_float2(val[k], val[k]));
@@ -409,7 +446,7 @@ __global__ void __launch_bounds__(NT, 2) k_grad_tofk(DevPlan P, int subset, cons
 // warp takes work units (32 consecutive radial bins of one view and plane group) from a
 // counter in device memory (cleared before the launch) until none is left, so that no SM
 // idles while a block waits for its slowest warp.
-template <int K, int WIN, int NT>
+template <int K, int WIN, int NT, bool ZI>
 __global__ void __launch_bounds__(NT, 2) k_grad_tofp(DevPlan P, int subset, const int *subset_dev,
                                                      const float *__restrict__ x, const float *__restrict__ xT,
                                                      float *__restrict__ g, float *__restrict__ gT,
@@ -442,7 +479,7 @@ __global__ void __launch_bounds__(NT, 2) k_grad_tofp(DevPlan P, int subset, cons
     const int r = chunk * 32 + lane;
     const bool ok = r < P.nrad;
     for (int k = 0; k < K * P.T; ++k) s_acc[k * NT + tid] = 0.f;
-    const double kl = tof_group<K, WIN, 1, NT>(P, s_tab, s_acc, v, ok ? r : 0, grp, ok, 0, tid, tid, x, xT, g, gT,
+    const double kl = tof_group<K, WIN, 1, NT, ZI>(P, s_tab, s_acc, v, ok ? r : 0, grp, ok, 0, tid, tid, x, xT, g, gT,
                                                mode, kl_part != nullptr);
     if (kl_part) s_kl[tid] += kl;
   }
@@ -483,7 +520,10 @@ static cudaError_t launch_tofk_t(const DevPlan &P, unsigned grid, int subset, co
   if (SPLIT == 1) {
     cudaError_t e = cudaMemsetAsync(P.tof_work, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    k_grad_tofp<K, WIN, NT><<<grid, NT, smem, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
+    if (K > 1 && P.tof_zint)
+      k_grad_tofp<K, WIN, NT, true><<<grid, NT, smem, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
+    else
+      k_grad_tofp<K, WIN, NT, false><<<grid, NT, smem, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
   } else {
     k_grad_tofk<K, WIN, SPLIT, NT><<<grid, NT, smem, st>>>(P, subset, subset_dev, x, xT, g, gT, kl_part, mode);
   }
@@ -496,7 +536,13 @@ template <int K, int WIN, int SPLIT>
 static cudaError_t tofk_attr() {
   constexpr int NT = tofk_nt<K>();
   const int bytes = (int)(kTofM * (WIN / 2) * sizeof(float4) + K * kTofMaxBins * NT * sizeof(float));
-  if (SPLIT == 1) return cudaFuncSetAttribute(k_grad_tofp<K, WIN, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (SPLIT == 1) {
+    cudaError_t e = cudaFuncSetAttribute(k_grad_tofp<K, WIN, NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         bytes);
+    if (e == cudaSuccess && K > 1)
+      e = cudaFuncSetAttribute(k_grad_tofp<K, WIN, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+  }
   return cudaFuncSetAttribute(k_grad_tofk<K, WIN, SPLIT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
