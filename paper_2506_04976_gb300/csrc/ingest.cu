@@ -50,6 +50,7 @@ extern "C" pet_status pet_copy_to_device(void *dst, const void *src, size_t byte
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return PET_ERR_CUDA;
+  if (ad.device != dev) return PET_ERR_ARG;  // dst on another device than the current one
   cudaStream_t st = (cudaStream_t)stream;
   const size_t n16 = bytes / 16;
   const int tail = (int)(bytes % 16);
