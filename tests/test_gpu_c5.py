@@ -32,6 +32,9 @@ def c5():
         plan = pet.Plan(p["geom"], p["nsub"])
         mu = torch.from_numpy(p["mu"].astype(np.float32)).to(DEV)
         plan.set_data(p["y"], p["r"], mu, p["sens"])
+        # the launch shape the autotuner picks at this size and the bench times: the
+        # persistent windowed TOF kernel with 2 planes per thread, one part per LOR
+        plan.set_grad_shape(2, 1)
         torch.cuda.synchronize()
         _S.update(p=p, plan=plan, mu=mu, gen_s=t1 - t0, setup_s=time.time() - t1)
     return _S
