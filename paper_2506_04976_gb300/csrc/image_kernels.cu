@@ -171,8 +171,11 @@ __global__ void __launch_bounds__(RDP_TX * RDP_TY) k_rdp_batch(const RdpJob *__r
   }
   __syncthreads();
   if (sub && __ldg(&sub[s_job]) == kBatchSkip) return;  // whole block: one job
-  rdp_body<false, true, false, false>(sj.a, sj.x, sj.grad, nullptr, nullptr, 0,
-                                      (int)blockIdx.x - __ldg(&begin[s_job]));
+  const int blk = (int)blockIdx.x - __ldg(&begin[s_job]);
+  if (sj.a.kappa)  // block-uniform: the job's kappa-weighted prior
+    rdp_body<true, true, false, false>(sj.a, sj.x, sj.grad, nullptr, nullptr, 0, blk);
+  else
+    rdp_body<false, true, false, false>(sj.a, sj.x, sj.grad, nullptr, nullptr, 0, blk);
 }
 
 cudaError_t launch_rdp_batch(const RdpJob *jobs, const int *begin, int njobs, int total_blocks,

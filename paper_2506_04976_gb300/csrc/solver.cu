@@ -1153,7 +1153,7 @@ extern "C" pet_status pet_batch_create(pet_solver *const *solvers, int n, int it
     if (si->o.algo != solvers[0]->o.algo || si->o.deterministic || si->o.low_memory ||
         si->o.sampling == PET_SAMPLE_IMPORTANCE)
       return PET_ERR_UNSUPPORTED;
-    if (si->plan->T != 1 || si->o.kappa) return PET_ERR_UNSUPPORTED;
+    if (si->plan->T != 1) return PET_ERR_UNSUPPORTED;
     for (int j = 0; j < i; ++j)
       if (solvers[j]->plan == si->plan || solvers[j] == si) return PET_ERR_ARG;  // scratch is per plan
     if (si->plan->res) return PET_ERR_UNSUPPORTED;  // batched launches read x directly

@@ -88,6 +88,52 @@ def test_batch_matches_single_runs_and_oracle(algo):
     assert np.linalg.norm(xb[1] - xo) <= 1e-4 * np.linalg.norm(xo)
 
 
+def test_batch_with_kappa_weighted_priors():
+    """Instances with a kappa image (eq. 3 weights) mixed with plain ones: each equals its
+    solver run alone, and the kappa-weighted 3D instance equals the oracle's trajectory."""
+    from paper_2506_04976_gb300 import binding as pet
+    inst = _instances()
+    kap = {}
+    for i in (1, 2):
+        shape = inst[i][1].img_shape
+        kap[i] = (0.5 + synth.random_image_like(inst[i][0]["geom"], 40 + i)).astype(np.float32).reshape(shape)
+    E, niter = 4, 3 * 4 + 7
+
+    def make(i, p, plan, x0):
+        n = p["nsub"]
+        kt = torch.from_numpy(kap[i]).to(DEV) if i in kap else None
+        s = pet.Solver(plan, algo=pet.SAGA, step_rule=pet.STEP_VANISH, tau0=1.0, eta=0.02, precond_kind=1,
+                       pc_iters=(0, n), beta=p["beta"], gamma=p["gamma"], eps=p["eps"], kappa=kt, seed=300 + i)
+        s._test_kappa = kt
+        s.set_image(torch.from_numpy(x0).to(DEV))
+        return s
+
+    solvers = [make(i, p, plan, x0) for i, (p, plan, _, _, x0) in enumerate(inst)]
+    b = pet.Batch(solvers, iters_per_graph=E)
+    b.set_grad_shape(2, 1)
+    b.run(niter)
+    torch.cuda.synchronize()
+    xb = [s.image().cpu().numpy().astype(np.float64) for s in solvers]
+    del b, solvers
+    for i, (p, plan, _, _, x0) in enumerate(inst):
+        plan.set_grad_shape(2, 1)
+        s1 = make(i, p, plan, x0)
+        s1.run(niter)
+        torch.cuda.synchronize()
+        x1 = s1.image().cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(xb[i] - x1) <= 1e-5 * np.linalg.norm(x1), i
+        del s1
+    p, plan, mu32, sens32, x0 = inst[1]
+    G = O.Geometry(p["geom"])
+    m = O.multiplicative(G, mu32, sens32)
+    n = p["nsub"]
+    xo, _, _ = O.solve(G, x0, m, p["r"], p["y"], O.sensitivity(G, 1, -1, m), algo=O.SAGA, nsub=n, niter=niter,
+                       order=O.subset_order(301, n, niter), step_rule=O.STEP_VANISH, tau0=1.0, eta=0.02,
+                       precond_kind=1, pc_iters=(0, n), beta=p["beta"], gamma=p["gamma"], eps=p["eps"],
+                       kappa=kap[1].astype(np.float64))
+    assert np.linalg.norm(xb[1] - xo) <= 1e-4 * np.linalg.norm(xo)
+
+
 def test_batch_autotune_and_shapes():
     from paper_2506_04976_gb300 import binding as pet
     inst = _instances()
