@@ -320,12 +320,13 @@ long long pet_solver_subsets(const pet_solver *s, int *subsets, long long cap);
  * instance whose window contains a preconditioner update or an SVRG snapshot refresh (n
  * subset gradients and a step), and every instance in a final window shorter than
  * iters_per_graph, runs that window alone (one iteration at a time, exactly as
- * pet_solver_run); the batched launches then skip it.  Requirements (else
- * PET_ERR_UNSUPPORTED / PET_ERR_ARG): SGD, SAGA or SVRG (all the same; SVRG with the
- * table and without importance sampling), non-TOF plans, no deterministic mode, no
- * resolution model, distinct plans (a plan's scratch serves one solver at a time).
- * Solvers with a kappa image (eq. 3 weights) and without one may be mixed.  The solvers
- * are borrowed. */
+ * pet_solver_run); the batched launches then skip it.  Instances whose options have no
+ * batched form (TOF plans, the deterministic backprojector, the table-free SVRG,
+ * importance sampling, the resolution model) run alone in every window, with the same
+ * results as pet_solver_run.  Solvers with a kappa image (eq. 3 weights) and without one
+ * are batched together.  Requirements (else PET_ERR_UNSUPPORTED / PET_ERR_ARG): one
+ * algorithm (SGD, SAGA or SVRG) for all, distinct plans (a plan's scratch serves one
+ * solver at a time).  The solvers are borrowed. */
 typedef struct pet_batch pet_batch;
 pet_status pet_batch_create(pet_solver *const *solvers, int n, int iters_per_graph, pet_batch **out);
 void pet_batch_destroy(pet_batch *b);

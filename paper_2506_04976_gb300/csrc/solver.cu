@@ -1121,6 +1121,7 @@ struct pet_batch {
   cudaStream_t side = nullptr;  // the prior's gradients, concurrent with the subset gradients
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::vector<char> after_single;  // instance ran its last iteration alone (accumulators to clear)
+  std::vector<char> solo;          // instance always runs alone (no batched form of its options)
   int rdp_zch = 0;                 // slices per batched RDP stencil block (0: each plan's own)
 };
 
@@ -1150,16 +1151,21 @@ extern "C" pet_status pet_batch_create(pet_solver *const *solvers, int n, int it
   for (int i = 0; i < n; ++i) {
     const pet_solver *si = solvers[i];
     if (!si) return PET_ERR_ARG;
-    if (si->o.algo != solvers[0]->o.algo || si->o.deterministic || si->o.low_memory ||
-        si->o.sampling == PET_SAMPLE_IMPORTANCE)
-      return PET_ERR_UNSUPPORTED;
-    if (si->plan->T != 1) return PET_ERR_UNSUPPORTED;
+    if (si->o.algo != solvers[0]->o.algo) return PET_ERR_UNSUPPORTED;
     for (int j = 0; j < i; ++j)
       if (solvers[j]->plan == si->plan || solvers[j] == si) return PET_ERR_ARG;  // scratch is per plan
-    if (si->plan->res) return PET_ERR_UNSUPPORTED;  // batched launches read x directly
   }
   pet_batch *b = new pet_batch();
   b->s.assign(solvers, solvers + n);
+  // options without a batched form run alone, one iteration at a time, inside every
+  // window: TOF plans, the deterministic backprojector, the table-free SVRG, importance
+  // sampling, the resolution model (the batched launches read x directly)
+  b->solo.assign(n, 0);
+  for (int i = 0; i < n; ++i) {
+    const pet_solver *si = solvers[i];
+    b->solo[i] = si->plan->T != 1 || si->o.deterministic || si->o.low_memory ||
+                 si->o.sampling == PET_SAMPLE_IMPORTANCE || si->plan->res;
+  }
   b->after_single.assign(n, 1);  // the solvers may have run alone before
   b->nj = n;
   b->E = iters_per_graph;
@@ -1222,11 +1228,12 @@ static pet_status batch_tables(pet_batch *b) {
     cj[i].a = s->g;
     cj[i].b = p->d_gT;
     cj[i].N = s->N;
-    gb[i + 1] = gb[i] + grad_blocks_shape(p->dp, p->vs_max, b->K, b->split);
     if (b->rdp_zch) rj[i].a.zch = b->rdp_zch;
-    rb[i + 1] = rb[i] + rdp_blocks(p->g.nx, p->g.ny, p->g.nz, rj[i].a.zch);
-    ub[i + 1] = ub[i] + ((p->g.nx + 31) / 32) * ((p->g.ny + 31) / 32) * p->g.nz;
-    cb[i + 1] = cb[i] + (int)std::max<size_t>(1, std::min<size_t>(256, (s->N / 4 + 255) / 256));
+    const bool on = !b->solo[i];  // instances that always run alone get no batched blocks
+    gb[i + 1] = gb[i] + (on ? grad_blocks_shape(p->dp, p->vs_max, b->K, b->split) : 0);
+    rb[i + 1] = rb[i] + (on ? rdp_blocks(p->g.nx, p->g.ny, p->g.nz, rj[i].a.zch) : 0);
+    ub[i + 1] = ub[i] + (on ? ((p->g.nx + 31) / 32) * ((p->g.ny + 31) / 32) * p->g.nz : 0);
+    cb[i + 1] = cb[i] + (on ? (int)std::max<size_t>(1, std::min<size_t>(256, (s->N / 4 + 255) / 256)) : 0);
   }
   b->gblocks = gb[n];
   b->rblocks = rb[n];
@@ -1361,8 +1368,10 @@ extern "C" pet_status pet_batch_autotune(pet_batch *b, void *stream, int *planes
   if (e != PET_OK) return e;
   e = batch_tables(b);
   if (e != PET_OK) return e;
-  note_launch();
-  k_clear_batch<<<b->cblocks, 256, 0, st>>>(b->d_cjobs, b->d_cbegin, b->nj, nullptr);  // discard the trial gradients
+  if (b->cblocks > 0) {
+    note_launch();
+    k_clear_batch<<<b->cblocks, 256, 0, st>>>(b->d_cjobs, b->d_cbegin, b->nj, nullptr);  // discard the trial gradients
+  }
   SCK(cudaGetLastError());
   SCK(cudaStreamSynchronize(st));
   if (planes_per_thread) *planes_per_thread = bk;
@@ -1398,7 +1407,7 @@ extern "C" pet_status pet_batch_run(pet_batch *b, long long niter, void *stream)
     const long long len = std::min<long long>(E, niter - done);
     int nalone = 0;
     for (int i = 0; i < n; ++i) {
-      alone[i] = len < E || window_has_event(b->s[i], b->s[i]->k, E);
+      alone[i] = b->solo[i] || len < E || window_has_event(b->s[i], b->s[i]->k, E);
       nalone += alone[i];
     }
     for (int i = 0; i < n; ++i) {

@@ -155,19 +155,61 @@ def test_batch_autotune_and_shapes():
             assert np.linalg.norm(a - c) <= 1e-5 * np.linalg.norm(a)
 
 
-def test_batch_rejects_shared_plans_and_unsupported_options():
+def test_batch_rejects_shared_plans_and_mixed_algorithms():
     from paper_2506_04976_gb300 import binding as pet
-    p, plan, _, _, x0 = _instances()[0]
+    inst = _instances()
+    p, plan, _, _, x0 = inst[0]
     s1 = _solver(pet, p, plan, x0, 1, pet.SAGA)
     s2 = _solver(pet, p, plan, x0, 2, pet.SAGA)
     with pytest.raises(pet.PetError):
         pet.Batch([s1, s2])
-    s3 = pet.Solver(plan, algo=pet.SVRG, beta=p["beta"], sampling=pet.SAMPLE_IMPORTANCE)
+    p2, plan2, _, _, x02 = inst[1]
+    s3 = _solver(pet, p2, plan2, x02, 3, pet.SGD)
     with pytest.raises(pet.PetError):
-        pet.Batch([s3])
-    s4 = pet.Solver(plan, algo=pet.SVRG, beta=p["beta"], low_memory=True)
-    with pytest.raises(pet.PetError):
-        pet.Batch([s4])
+        pet.Batch([s1, s3])
+
+
+def test_batch_runs_unbatched_options_alone():
+    """A TOF plan, the deterministic backprojector and the table-free SVRG have no batched
+    form: inside a batch they run alone in every window and give the results of the same
+    solvers run on their own, while the other instances stay batched."""
+    from paper_2506_04976_gb300 import binding as pet
+    inst = _instances()
+    pt = synth.make_problem("c3", 21, nx=24, nz=7, nrad=40, nview=24, nsub=4)
+    plan_t = pet.Plan(pt["geom"], pt["nsub"])
+    plan_t.set_data(torch.from_numpy(pt["y"].astype(np.int32)).to(DEV), torch.from_numpy(pt["r"]).to(DEV),
+                    torch.from_numpy(pt["mu"].astype(np.float32)).to(DEV),
+                    torch.from_numpy(pt["sens"].astype(np.float32)).to(DEV))
+    x0t = np.full(plan_t.img_shape, float(pt["x_true"].mean()), np.float32)
+    cases = [(inst[0][0], inst[0][1], inst[0][4], {}), (inst[1][0], inst[1][1], inst[1][4], {}),
+             (inst[2][0], inst[2][1], inst[2][4], dict(deterministic=True)), (pt, plan_t, x0t, {}),
+             (inst[3][0], inst[3][1], inst[3][4], dict(low_memory=True))]
+
+    def make(i, p, plan, x0, extra):
+        n = p["nsub"]
+        s = pet.Solver(plan, algo=pet.SVRG, step_rule=pet.STEP_VANISH, tau0=1.0, eta=0.02, precond_kind=1,
+                       pc_iters=(0, n), beta=p["beta"], gamma=p["gamma"], eps=p["eps"], seed=400 + i, **extra)
+        s.set_image(torch.from_numpy(x0).to(DEV))
+        return s
+
+    niter = 3 * 4 + 6
+    solvers = [make(i, *c) for i, c in enumerate(cases)]
+    b = pet.Batch(solvers, iters_per_graph=4)
+    b.set_grad_shape(2, 1)
+    b.run(niter)
+    torch.cuda.synchronize()
+    xb = [s.image().cpu().numpy().astype(np.float64) for s in solvers]
+    del b, solvers
+    for i, (p, plan, x0, extra) in enumerate(cases):
+        plan.set_grad_shape(2, 1)
+        s1 = make(i, p, plan, x0, extra)
+        s1.run(niter)
+        torch.cuda.synchronize()
+        x1 = s1.image().cpu().numpy().astype(np.float64)
+        if extra.get("deterministic"):
+            assert np.array_equal(xb[i], x1), i  # the voxel-driven gather has a fixed order
+        else:
+            assert np.linalg.norm(xb[i] - x1) <= 1e-5 * np.linalg.norm(x1), i
 
 
 def test_c4_specs_shape():

@@ -9,7 +9,9 @@ runs start from identical values.  Bounds: 1e-4 relative L2 over the phantom sup
 
 c4 (32 instances of uneven image and sinogram sizes, betas, count levels and subset
 counts, as generated by synth.batch_specs): SAGA advanced by the batched driver equals
-every instance run alone, and the smallest instance equals the oracle's trajectory."""
+every instance run alone (within 1e-5, or within twice the difference between two single
+runs where the atomics' order alone moves a low-count instance further), and the
+smallest instance equals the oracle's trajectory."""
 import multiprocessing as mp
 import os
 
@@ -110,10 +112,18 @@ def test_c4_batch_of_32_matches_single_runs_and_oracle():
         s1.run(niter)
         torch.cuda.synchronize()
         x1 = s1.image().cpu().numpy().astype(np.float64)
-        assert np.linalg.norm(xb[i] - x1) <= 1e-5 * np.linalg.norm(x1), i
+        # the FP32 atomics add in a different order in every run, batched or not: the
+        # bound is 1e-5 or, where a second single run differs from the first by more
+        # (low-count instances amplify the rounding over the iterations), twice that
+        # run-to-run difference
+        s2 = _saga(pet, p, plan, x0, 500 + i)
+        s2.run(niter)
+        torch.cuda.synchronize()
+        d_ss = np.linalg.norm(s2.image().cpu().numpy().astype(np.float64) - x1)
+        assert np.linalg.norm(xb[i] - x1) <= max(1e-5 * np.linalg.norm(x1), 2.0 * d_ss), i
         assert np.array_equal(taus_b[i], s1.taus()) and np.array_equal(subs_b[i], s1.subsets()), i
         assert np.array_equal(subs_b[i], O.subset_order(500 + i, p["nsub"], niter)), i
-        del s1
+        del s1, s2
     i = min(range(len(inst)), key=lambda k: inst[k][1].N * len(inst[k][0]["geom"]["z1"]))
     p, plan, mu32, sens32, x0 = inst[i]
     G = O.Geometry(p["geom"])
